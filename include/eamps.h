@@ -1,0 +1,221 @@
+/*
+ * eamps.h -- C ABI of the GB300 entanglement-aware MPS / MPO two-site update.
+ *
+ * The library simulates a quantum circuit of nearest-neighbour gates on a
+ * matrix product state (pure states, local dimension 2, Eq. (mps) of the
+ * paper) or on a vectorised matrix product operator (mixed states, local
+ * dimension 4, Eq. (mpo)).  Every two-qubit gate runs the hot path of the
+ * entanglement-aware algorithm ("Entanglement-aware simulations" section):
+ *   move the orthogonality centre onto the gate pair (canonical form,
+ *   "Canonicalization" section), contract the two site tensors with the
+ *   gate into theta, take the SVD of theta, keep the smallest bond whose
+ *   truncation fidelity (Eq. fT-pure / Eq. fT-mixed) is not lower than the
+ *   target, and multiply the running product of truncation fidelities
+ *   (Eq. prod), which is the inferred state fidelity.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Operators on the API are row-major complex matrices of doubles stored as
+ *    interleaved (re, im) pairs: a d x d matrix is 2*d*d doubles.
+ *  - Qubits are numbered 0..N-1 along the chain.  A two-qubit operator acts on
+ *    (q, q+1) in the basis |s_q s_{q+1}>, s_q the more significant index.
+ *  - Mixed states: the local index of an MPO site is t = 2 s + s' for the
+ *    operator |s><s'|.  A superoperator of a channel {K} on n_q qubits is the
+ *    4^n_q x 4^n_q matrix S[(t_1..), (u_1..)] = sum_K K[(s..),(r..)] conj(K[(s'..),(r'..)])
+ *    with t_i = 2 s_i + s'_i, u_i = 2 r_i + r'_i (see mps_superop_from_kraus).
+ *  - Ownership: host buffers passed in are borrowed and fully read (or
+ *    written) before the call returns.  All device memory is owned by the
+ *    handle and released by mps_destroy.  Pointers documented as "device"
+ *    must point to memory of the handle's device.
+ *  - Streams: all GPU work of a handle is ordered on the CUDA stream given to
+ *    mps_create (NULL = the legacy default stream).
+ *  - Errors: no exception crosses the ABI.  Every call returns an mps_status.
+ *    GPU-side failures (non-convergence, non-finite values, a wait that timed
+ *    out) are recorded in a sticky status word and returned by this and every
+ *    later call of the handle.  One handle must not be used by two host
+ *    threads at once.
+ */
+#ifndef EAMPS_H
+#define EAMPS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mps_state* mps_handle;
+
+typedef enum {
+  MPS_OK = 0,
+  MPS_ERR_ARG = 1,            /* invalid argument (sizes, qubit index, operator dimension) */
+  MPS_ERR_NONADJACENT = 2,    /* a two-qubit gate on non-neighbouring qubits (linear nearest-neighbour only) */
+  MPS_ERR_OOM = 3,            /* device or host allocation failed */
+  MPS_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  MPS_ERR_NOT_CONVERGED = 5,  /* the Jacobi SVD reached max_sweeps */
+  MPS_ERR_NONFINITE = 6,      /* a singular value or a weight was NaN / Inf */
+  MPS_WARN_CHI_CAP = 7,       /* the bond cap bound a truncation: the fidelity target is no longer guaranteed */
+  MPS_ERR_TIMEOUT = 8,        /* a device-side wait gave up (bounded spin); the handle is unusable */
+  MPS_ERR_STATE = 9           /* call not valid in the current state (e.g. after a sticky error) */
+} mps_status;
+
+enum { MPS_PURE = 0, MPS_MIXED = 1 };                          /* mps_options.kind */
+enum { MPS_NAIVE = 0, MPS_GLOBAL = 1, MPS_NEAREST = 2 };       /* mps_options.strategy */
+enum { MPS_FP64 = 0, MPS_TF32X3 = 1, MPS_FP32 = 2 };           /* mps_options.precision */
+enum { MPS_KEPT_RATIO = 0, MPS_WANG_SQRT = 1 };                /* mps_options.mixed_fid */
+
+typedef struct {
+  int kind;             /* MPS_PURE (d = 2) or MPS_MIXED (d = 4) */
+  double f_min;         /* final fidelity to reach, F_min of Eq. (uniform); >= 1 disables truncation */
+  long long n_2q;       /* number of two-qubit gates of the circuit, known in advance (Eq. uniform) */
+  int strategy;         /* target schedule: MPS_NAIVE, MPS_GLOBAL (default), MPS_NEAREST (Fig. 1) */
+  int chi_max;          /* cap on every bond (0 = no cap beyond 1024); the paper's advised cap */
+  int fixed_chi;        /* > 0: standard fixed-maximum truncation k = min(fixed_chi, rank bound) */
+  int precision;        /* MPS_TF32X3 (complex64, tensor-core 3xTF32 contractions, default),
+                           MPS_FP32 (complex64, CUDA-core contractions), MPS_FP64 (complex128 throughout) */
+  int mixed_fid;        /* MPO truncation fidelity: MPS_KEPT_RATIO f = W_k/W (default), MPS_WANG_SQRT f = sqrt(W_k/W) */
+  int max_sweeps;       /* Jacobi sweep limit (default 40) */
+  int log_truncations;  /* keep a host-side record of every truncation (default 1) */
+} mps_options;
+
+/* One record per two-qubit gate: bond size kept, truncation fidelity f, the
+ * target f_t it was chosen against, total weight W = sum s_i^2 and kept
+ * weight W_k (both FP64), and the rank bound min(rows, cols) of theta. */
+typedef struct {
+  int q;
+  int k;
+  int rank_bound;
+  int cap_hit;
+  double f;
+  double f_t;
+  double W;
+  double W_k;
+} mps_trunc_record;
+
+/* Fill *opt with the defaults listed above.  Never fails. */
+void mps_default_options(mps_options* opt);
+
+/* Human-readable name of a status code (static string; never NULL). */
+const char* mps_status_string(mps_status s);
+
+/* Create the product state |0...0> (PURE) or |0...0><0...0| (MIXED) on
+ * n_qubits >= 2 qubits, on the current CUDA device, ordered on cuda_stream
+ * (a cudaStream_t; NULL = default stream).  Allocates the site arena for the
+ * largest bonds the options allow (min(cap, d^min(i, N-i)) per bond i) and
+ * the scratch of the two-site update.  The uniform target f0 = F_min^(1/n_2q)
+ * of Eq. (uniform) is set here.  *out receives the handle, or NULL on error.
+ * Errors: MPS_ERR_ARG (n_qubits < 2, bad option values, NULL out/opt),
+ * MPS_ERR_OOM, MPS_ERR_CUDA. */
+mps_status mps_create(mps_handle* out, int n_qubits, const mps_options* opt, void* cuda_stream);
+
+/* Release all device and host memory of the handle (waits for its stream).
+ * NULL is accepted and ignored. */
+mps_status mps_destroy(mps_handle h);
+
+/* Apply a single-qubit operator to qubit q ("The matrix product formalism":
+ * single-qubit gates do not change any bond).  op: host, 2*op_dim*op_dim
+ * doubles.  PURE: op_dim = 2, a unitary; applied in place on site q.
+ * MIXED: op_dim = 2 (a unitary U, applied as U rho U^dagger) or 4 (a
+ * superoperator); the centre is moved to q first so that the canonical form
+ * survives a non-unitary channel, and the norm change is folded into the
+ * FP64 log-norm.  Errors: MPS_ERR_ARG. */
+mps_status mps_apply_1q(mps_handle h, int q, const double* op, int op_dim);
+
+/* The hot path: apply a two-qubit operator to (q, q+1) and truncate the bond
+ * between them ("Truncation fidelity" and "Entanglement-aware simulations"
+ * sections).  op: host, 2*op_dim*op_dim doubles; PURE: op_dim = 4 (unitary);
+ * MIXED: op_dim = 4 (unitary, applied as U rho U^dagger) or 16
+ * (superoperator, e.g. a gate followed by noise).
+ * target < 0: use the schedule of mps_options (Eq. uniform and Fig. 1);
+ * target >= 1: keep every singular value (no cut); otherwise the
+ * per-truncation target f_t for this gate.  The schedule counter advances in
+ * every case.  The call returns after the truncation is decided (the chosen
+ * bond is read back); kernels of later calls overlap nothing of this one.
+ * Errors: MPS_ERR_ARG, MPS_ERR_NONADJACENT is not possible by construction
+ * (the pair is always (q, q+1)); q must satisfy 0 <= q < N-1. */
+mps_status mps_apply_2q(mps_handle h, int q, const double* op, int op_dim, double target);
+
+/* As mps_apply_2q, but op_dev points to the operator in DEVICE memory
+ * (2*op_dim*op_dim doubles, same layout), e.g. a whole circuit uploaded
+ * once.  The pointer must stay valid until the call returns. */
+mps_status mps_apply_2q_device(mps_handle h, int q, const double* op_dev, int op_dim, double target);
+
+/* Apply n_gates two-qubit gates: gate g acts on (qs[g], qs[g]+1) (qs: host)
+ * with the operator at ops_dev + g*2*op_dim*op_dim (DEVICE doubles).  Same
+ * target semantics as mps_apply_2q for every gate.  Stops at the first error. */
+mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev,
+                                    int op_dim, double target);
+
+/* *inferred = running product of truncation fidelities (Eq. prod), FP64. */
+mps_status mps_fidelity(mps_handle h, double* inferred);
+
+/* PURE: <psi|O|psi>, computed from the canonical form with only the tensors
+ * on the support ("Canonicalization" section; the centre is moved onto the
+ * support).  MIXED: Tr(O rho)/Tr(rho) by a transfer contraction along the
+ * chain.  support = 1 (O on q, op_dim 2) or 2 (O on (q, q+1), op_dim 4).
+ * op: host row-major complex; out_re_im: host, 2 doubles. */
+mps_status mps_expect(mps_handle h, int q, int support, const double* op, double* out_re_im);
+
+/* PURE: <b|psi>.  MIXED: <b|rho|b> / Tr(rho).  bits: host, N bytes (0/1),
+ * qubit 0 first.  out_re_im: host, 2 doubles. */
+mps_status mps_amplitude(mps_handle h, const unsigned char* bits, double* out_re_im);
+
+/* Current bonds (N-1 ints, bond i between qubits i and i+1). */
+mps_status mps_bond_dims(mps_handle h, int* out);
+
+/* Orthogonality centre (site index). */
+mps_status mps_centre(mps_handle h, int* out);
+
+/* Copy site tensor i to the host as complex128, shape (chi_L, d, chi_R)
+ * row-major, 2*chi_L*d*chi_R doubles; dims3 (host, 3 ints) receives the
+ * shape.  Errors: MPS_ERR_ARG if cap (in doubles) is too small. */
+mps_status mps_get_site(mps_handle h, int i, double* out, long long cap, int* dims3);
+
+/* FP64 log of the norm factor of an MPO (rho = exp(lognorm) * stored rho). */
+mps_status mps_lognorm(mps_handle h, double* out);
+
+/* Singular values of the last two-qubit gate, in decreasing order (FP64),
+ * all rank_bound of them.  *count receives how many were written (at most cap). */
+mps_status mps_last_singular_values(mps_handle h, double* out, int cap, int* count);
+
+/* Copy up to cap truncation records (oldest first); *count receives the number copied. */
+mps_status mps_truncation_log(mps_handle h, mps_trunc_record* out, int cap, int* count);
+
+/* Wait for all queued work of the handle and return its sticky status. */
+mps_status mps_sync(mps_handle h);
+
+/* Return the handle to its initial product state and reset the fidelity
+ * product, the schedule counter, the log-norm, the truncation log and the
+ * sticky status, keeping every allocation (so that repeated runs allocate
+ * nothing).  Errors: MPS_ERR_CUDA. */
+mps_status mps_reset(mps_handle h);
+
+/* Kernel statistics of a handle, accumulated since the last mps_stats_reset.
+ * Durations come from CUDA events recorded on the handle's stream around the
+ * launches of the Jacobi SVD and of the contractions when profiling is on
+ * (mps_profile); counts are always kept. */
+typedef struct {
+  long long kernel_launches;   /* every kernel this library launched */
+  long long jacobi_launches;
+  long long jacobi_sweeps;     /* sweeps summed over launches */
+  double jacobi_ms;            /* summed event durations (profiling on) */
+  double jacobi_flops;         /* algorithmic FP flops of the Jacobi launches (see DESIGN) */
+  long long gemm_launches;
+  double gemm_ms;
+  double gemm_flops;           /* 8 M N K per complex GEMM */
+  long long gates;             /* two-qubit updates applied */
+} mps_stats_t;
+
+/* Switch event timing of the Jacobi and contraction launches on (1) or off (0). */
+mps_status mps_profile(mps_handle h, int on);
+mps_status mps_stats(mps_handle h, mps_stats_t* out);
+mps_status mps_stats_reset(mps_handle h);
+
+/* Host helper: the superoperator of the channel {K} (n_kraus operators of
+ * dimension 2^nq, host, 2*4^nq doubles each, concatenated) in the library's
+ * vectorisation convention (see the top of this file).  out: host,
+ * 2*16^nq doubles.  nq = 1 or 2.  Errors: MPS_ERR_ARG. */
+mps_status mps_superop_from_kraus(const double* kraus, int n_kraus, int nq, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EAMPS_H */

@@ -1,0 +1,360 @@
+"""GB300-native entanglement-aware MPS / MPO simulation (arXiv:2307.16870 hot path).
+
+Thin ctypes binding of ``libeamps.so`` (C ABI declared in ``include/eamps.h``).
+Every step of the two-site update runs in the library's CUDA kernels; this
+module only marshals arguments.  Importing it loads the library; when the
+library is missing or cannot be loaded, the import fails loudly (there is no
+CPU fallback).
+
+Functions carry the C names (``mps_create``, ``mps_apply_2q``, ...).  The
+class :class:`MPS` is a convenience wrapper over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, build
+
+__all__ = [
+    "PURE", "MIXED", "NAIVE", "GLOBAL", "NEAREST", "FP64", "TF32X3", "FP32", "KEPT_RATIO", "WANG_SQRT",
+    "MpsError", "MpsOptions", "TruncRecord", "load", "lib", "MPS",
+    "mps_default_options", "mps_create", "mps_destroy", "mps_apply_1q", "mps_apply_2q",
+    "mps_apply_2q_device", "mps_apply_circuit_device", "mps_fidelity", "mps_expect", "mps_amplitude",
+    "mps_bond_dims", "mps_centre", "mps_get_site", "mps_lognorm", "mps_last_singular_values",
+    "mps_truncation_log", "mps_sync", "mps_superop_from_kraus", "mps_status_string",
+    "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats",
+]
+
+PURE, MIXED = 0, 1
+NAIVE, GLOBAL, NEAREST = 0, 1, 2
+FP64, TF32X3, FP32 = 0, 1, 2
+KEPT_RATIO, WANG_SQRT = 0, 1
+
+OK, WARN_CHI_CAP = 0, 7
+
+# The tensor-core (tcgen05) contraction path of precision TF32X3.
+TC_AVAILABLE = False
+
+
+class MpsOptions(C.Structure):
+    _fields_ = [("kind", C.c_int), ("f_min", C.c_double), ("n_2q", C.c_longlong), ("strategy", C.c_int),
+                ("chi_max", C.c_int), ("fixed_chi", C.c_int), ("precision", C.c_int), ("mixed_fid", C.c_int),
+                ("max_sweeps", C.c_int), ("log_truncations", C.c_int)]
+
+
+class TruncRecord(C.Structure):
+    _fields_ = [("q", C.c_int), ("k", C.c_int), ("rank_bound", C.c_int), ("cap_hit", C.c_int),
+                ("f", C.c_double), ("f_t", C.c_double), ("W", C.c_double), ("W_k", C.c_double)]
+
+
+class MpsStats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_longlong), ("jacobi_launches", C.c_longlong),
+                ("jacobi_sweeps", C.c_longlong), ("jacobi_ms", C.c_double), ("jacobi_flops", C.c_double),
+                ("gemm_launches", C.c_longlong), ("gemm_ms", C.c_double), ("gemm_flops", C.c_double),
+                ("gates", C.c_longlong)]
+
+
+class MpsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {mps_status_string(code)} (status {code})")
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libeamps.so (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        build()
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    D = C.POINTER(C.c_double)
+    sig = {
+        "mps_default_options": (None, [C.POINTER(MpsOptions)]),
+        "mps_status_string": (C.c_char_p, [C.c_int]),
+        "mps_create": (C.c_int, [C.POINTER(H), C.c_int, C.POINTER(MpsOptions), C.c_void_p]),
+        "mps_destroy": (C.c_int, [H]),
+        "mps_apply_1q": (C.c_int, [H, C.c_int, D, C.c_int]),
+        "mps_apply_2q": (C.c_int, [H, C.c_int, D, C.c_int, C.c_double]),
+        "mps_apply_2q_device": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int, C.c_double]),
+        "mps_apply_circuit_device": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_int, C.c_double]),
+        "mps_fidelity": (C.c_int, [H, D]),
+        "mps_expect": (C.c_int, [H, C.c_int, C.c_int, D, D]),
+        "mps_amplitude": (C.c_int, [H, C.POINTER(C.c_ubyte), D]),
+        "mps_bond_dims": (C.c_int, [H, C.POINTER(C.c_int)]),
+        "mps_centre": (C.c_int, [H, C.POINTER(C.c_int)]),
+        "mps_get_site": (C.c_int, [H, C.c_int, D, C.c_longlong, C.POINTER(C.c_int)]),
+        "mps_lognorm": (C.c_int, [H, D]),
+        "mps_last_singular_values": (C.c_int, [H, D, C.c_int, C.POINTER(C.c_int)]),
+        "mps_truncation_log": (C.c_int, [H, C.POINTER(TruncRecord), C.c_int, C.POINTER(C.c_int)]),
+        "mps_sync": (C.c_int, [H]),
+        "mps_superop_from_kraus": (C.c_int, [D, C.c_int, C.c_int, D]),
+        "mps_reset": (C.c_int, [H]),
+        "mps_profile": (C.c_int, [H, C.c_int]),
+        "mps_stats": (C.c_int, [H, C.POINTER(MpsStats)]),
+        "mps_stats_reset": (C.c_int, [H]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib():
+    return load()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _cplx(op) -> np.ndarray:
+    """Row-major complex matrix -> contiguous interleaved doubles (kept alive by the caller)."""
+    return np.ascontiguousarray(np.asarray(op, dtype=np.complex128)).view(np.float64).reshape(-1)
+
+
+def _check(code: int, where: str, allow_warn: bool = True) -> int:
+    if code == OK or (allow_warn and code == WARN_CHI_CAP):
+        return code
+    raise MpsError(code, where)
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def mps_status_string(code: int) -> str:
+    return load().mps_status_string(int(code)).decode()
+
+
+def mps_default_options() -> MpsOptions:
+    o = MpsOptions()
+    load().mps_default_options(C.byref(o))
+    return o
+
+
+def mps_create(n_qubits: int, opt: MpsOptions, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().mps_create(C.byref(h), int(n_qubits), C.byref(opt), C.c_void_p(stream or None)), "mps_create")
+    return h.value
+
+
+def mps_destroy(h: int) -> None:
+    load().mps_destroy(C.c_void_p(h))
+
+
+def mps_apply_1q(h: int, q: int, op) -> int:
+    a = _cplx(op)
+    dim = int(round((a.size // 2) ** 0.5))
+    return _check(load().mps_apply_1q(C.c_void_p(h), int(q), _dptr(a), dim), "mps_apply_1q")
+
+
+def mps_apply_2q(h: int, q: int, op, target: float = -1.0) -> int:
+    a = _cplx(op)
+    dim = int(round((a.size // 2) ** 0.5))
+    return _check(load().mps_apply_2q(C.c_void_p(h), int(q), _dptr(a), dim, float(target)), "mps_apply_2q")
+
+
+def mps_apply_2q_device(h: int, q: int, op_dev_ptr: int, op_dim: int, target: float = -1.0) -> int:
+    return _check(load().mps_apply_2q_device(C.c_void_p(h), int(q), C.c_void_p(op_dev_ptr), int(op_dim),
+                                             float(target)), "mps_apply_2q_device")
+
+
+def mps_apply_circuit_device(h: int, qs, ops_dev_ptr: int, op_dim: int, target: float = -1.0) -> int:
+    q = np.ascontiguousarray(np.asarray(qs, dtype=np.int32))
+    return _check(load().mps_apply_circuit_device(C.c_void_p(h), int(q.size), q.ctypes.data_as(C.POINTER(C.c_int)),
+                                                  C.c_void_p(ops_dev_ptr), int(op_dim), float(target)),
+                  "mps_apply_circuit_device")
+
+
+def mps_fidelity(h: int) -> float:
+    v = C.c_double()
+    _check(load().mps_fidelity(C.c_void_p(h), C.byref(v)), "mps_fidelity")
+    return v.value
+
+
+def mps_expect(h: int, q: int, op) -> complex:
+    a = _cplx(op)
+    dim = int(round((a.size // 2) ** 0.5))
+    out = np.zeros(2)
+    _check(load().mps_expect(C.c_void_p(h), int(q), 1 if dim == 2 else 2, _dptr(a), _dptr(out)), "mps_expect")
+    return complex(out[0], out[1])
+
+
+def mps_amplitude(h: int, bits) -> complex:
+    b = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8))
+    out = np.zeros(2)
+    _check(load().mps_amplitude(C.c_void_p(h), b.ctypes.data_as(C.POINTER(C.c_ubyte)), _dptr(out)), "mps_amplitude")
+    return complex(out[0], out[1])
+
+
+def mps_bond_dims(h: int, n_qubits: int) -> list[int]:
+    out = (C.c_int * max(n_qubits - 1, 1))()
+    _check(load().mps_bond_dims(C.c_void_p(h), out), "mps_bond_dims")
+    return list(out)[: n_qubits - 1]
+
+
+def mps_centre(h: int) -> int:
+    v = C.c_int()
+    _check(load().mps_centre(C.c_void_p(h), C.byref(v)), "mps_centre")
+    return v.value
+
+
+def mps_get_site(h: int, i: int, max_elems: int) -> np.ndarray:
+    buf = np.zeros(2 * max_elems)
+    dims = (C.c_int * 3)()
+    _check(load().mps_get_site(C.c_void_p(h), int(i), _dptr(buf), buf.size, dims), "mps_get_site")
+    n = dims[0] * dims[1] * dims[2]
+    return buf[: 2 * n].view(np.complex128).reshape(dims[0], dims[1], dims[2]).copy()
+
+
+def mps_lognorm(h: int) -> float:
+    v = C.c_double()
+    _check(load().mps_lognorm(C.c_void_p(h), C.byref(v)), "mps_lognorm")
+    return v.value
+
+
+def mps_last_singular_values(h: int, cap: int = 1 << 14) -> np.ndarray:
+    buf = np.zeros(cap)
+    cnt = C.c_int()
+    _check(load().mps_last_singular_values(C.c_void_p(h), _dptr(buf), cap, C.byref(cnt)), "mps_last_singular_values")
+    return buf[: cnt.value].copy()
+
+
+def mps_truncation_log(h: int, cap: int = 1 << 20) -> list[dict]:
+    arr = (TruncRecord * cap)()
+    cnt = C.c_int()
+    _check(load().mps_truncation_log(C.c_void_p(h), arr, cap, C.byref(cnt)), "mps_truncation_log")
+    return [{"q": r.q, "k": r.k, "rank_bound": r.rank_bound, "cap_hit": r.cap_hit, "f": r.f, "f_t": r.f_t,
+             "W": r.W, "W_k": r.W_k} for r in arr[: cnt.value]]
+
+
+def mps_sync(h: int) -> int:
+    return _check(load().mps_sync(C.c_void_p(h)), "mps_sync")
+
+
+def mps_reset(h: int) -> int:
+    return _check(load().mps_reset(C.c_void_p(h)), "mps_reset")
+
+
+def mps_profile(h: int, on: bool) -> int:
+    return _check(load().mps_profile(C.c_void_p(h), int(bool(on))), "mps_profile")
+
+
+def mps_stats(h: int) -> dict:
+    st = MpsStats()
+    _check(load().mps_stats(C.c_void_p(h), C.byref(st)), "mps_stats")
+    return {name: getattr(st, name) for name, _ in MpsStats._fields_}
+
+
+def mps_stats_reset(h: int) -> int:
+    return _check(load().mps_stats_reset(C.c_void_p(h)), "mps_stats_reset")
+
+
+def mps_superop_from_kraus(kraus: list, nq: int) -> np.ndarray:
+    ks = np.concatenate([_cplx(k) for k in kraus])
+    out = np.zeros(2 * 16 ** nq)
+    _check(load().mps_superop_from_kraus(_dptr(ks), len(kraus), int(nq), _dptr(out)), "mps_superop_from_kraus")
+    d = 4 ** nq
+    return out.view(np.complex128).reshape(d, d).copy()
+
+
+# ---------------------------------------------------------------- convenience class
+class MPS:
+    """One EA-MPS (kind=PURE) or EA-MPO (kind=MIXED) handle on the current CUDA device."""
+
+    def __init__(self, n_qubits: int, kind: int = PURE, f_min: float = 1.0, n_2q: int = 0,
+                 strategy: int = GLOBAL, chi_max: int = 0, fixed_chi: int = 0, precision: int = TF32X3,
+                 mixed_fid: int = KEPT_RATIO, max_sweeps: int = 40, log_truncations: bool = True,
+                 stream: int = 0):
+        o = mps_default_options()
+        o.kind, o.f_min, o.n_2q, o.strategy = kind, f_min, n_2q, strategy
+        o.chi_max, o.fixed_chi, o.precision, o.mixed_fid = chi_max, fixed_chi, precision, mixed_fid
+        o.max_sweeps, o.log_truncations = max_sweeps, int(log_truncations)
+        self.n = n_qubits
+        self.kind = kind
+        self.d = 2 if kind == PURE else 4
+        self.h = mps_create(n_qubits, o, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_1q(self, q, op):
+        return mps_apply_1q(self.h, q, op)
+
+    def apply_2q(self, q, op, target=-1.0):
+        return mps_apply_2q(self.h, q, op, target)
+
+    def run(self, gates, target=-1.0):
+        for q, u in gates:
+            mps_apply_2q(self.h, q, u, target)
+        return self
+
+    def fidelity(self):
+        return mps_fidelity(self.h)
+
+    def expect(self, q, op):
+        return mps_expect(self.h, q, op)
+
+    def amplitude(self, bits):
+        return mps_amplitude(self.h, bits)
+
+    def bond_dims(self):
+        return mps_bond_dims(self.h, self.n)
+
+    def centre(self):
+        return mps_centre(self.h)
+
+    def site(self, i):
+        b = [1] + self.bond_dims() + [1]
+        return mps_get_site(self.h, i, b[i] * self.d * b[i + 1])
+
+    def lognorm(self):
+        return mps_lognorm(self.h)
+
+    def last_singular_values(self):
+        return mps_last_singular_values(self.h)
+
+    def truncation_log(self):
+        return mps_truncation_log(self.h)
+
+    def sync(self):
+        return mps_sync(self.h)
+
+    def reset(self):
+        return mps_reset(self.h)
+
+    def profile(self, on=True):
+        return mps_profile(self.h, on)
+
+    def stats(self):
+        return mps_stats(self.h)
+
+    def stats_reset(self):
+        return mps_stats_reset(self.h)
+
+    def contract(self) -> np.ndarray:
+        """All sites contracted on the host (test helper): d^N coefficients."""
+        t = self.site(0).reshape(self.d, -1)
+        for i in range(1, self.n):
+            b = self.site(i)
+            t = (t @ b.reshape(b.shape[0], -1)).reshape(-1, b.shape[2])
+        return t.reshape(-1)
+
+
+load()

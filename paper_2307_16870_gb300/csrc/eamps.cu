@@ -1,0 +1,838 @@
+// C ABI of the entanglement-aware MPS / MPO library and the host-side
+// orchestration of the two-site update.  Every numerical step runs in the
+// device kernels of this directory; the host plans launches, tracks the bond
+// sizes it reads back after each truncation, and marshals arguments.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "eamps.h"
+#include "gemm_tc.h"
+#include "kernels.h"
+
+using namespace eamps;
+
+namespace {
+
+constexpr int kDefaultCap = 1024;
+
+mps_status from_bits(int bits) {
+  if (bits & ST_TIMEOUT) return MPS_ERR_TIMEOUT;
+  if (bits & ST_NONFINITE) return MPS_ERR_NONFINITE;
+  if (bits & ST_NOT_CONVERGED) return MPS_ERR_NOT_CONVERGED;
+  if (bits & ST_BAD_ARG) return MPS_ERR_ARG;
+  return MPS_OK;
+}
+
+// Superoperator of the channel {K} in the vectorisation t = 2 s + s' per qubit, qubit 0 major:
+// S[(t..),(u..)] = sum_K K[(s..),(r..)] conj(K[(s'..),(r'..)]).
+void superop_from_kraus_host(const double* kraus, int n_kraus, int nq, double* out) {
+  const int dim = 1 << nq;
+  const int D = dim * dim;
+  std::memset(out, 0, sizeof(double) * 2 * D * D);
+  for (int kk = 0; kk < n_kraus; ++kk) {
+    const double* K = kraus + (size_t)kk * 2 * dim * dim;
+    for (int s = 0; s < dim; ++s)
+      for (int sp = 0; sp < dim; ++sp)
+        for (int r = 0; r < dim; ++r)
+          for (int rp = 0; rp < dim; ++rp) {
+            const double ar = K[2 * (s * dim + r)], ai = K[2 * (s * dim + r) + 1];
+            const double br = K[2 * (sp * dim + rp)], bi = -K[2 * (sp * dim + rp) + 1];
+            const double vr = ar * br - ai * bi, vi = ar * bi + ai * br;
+            int t = 0, u = 0;
+            for (int qb = 0; qb < nq; ++qb) {
+              const int sh = nq - 1 - qb;
+              t = t * 4 + 2 * ((s >> sh) & 1) + ((sp >> sh) & 1);
+              u = u * 4 + 2 * ((r >> sh) & 1) + ((rp >> sh) & 1);
+            }
+            out[2 * (t * D + u)] += vr;
+            out[2 * (t * D + u) + 1] += vi;
+          }
+  }
+}
+
+}  // namespace
+
+struct mps_state {
+  virtual ~mps_state() {}
+  virtual mps_status apply_1q(int q, const double* op, int op_dim) = 0;
+  virtual mps_status apply_2q(int q, const double* op, bool on_device, int op_dim, double target) = 0;
+  virtual mps_status fidelity(double* out) = 0;
+  virtual mps_status expect(int q, int support, const double* op, double* out) = 0;
+  virtual mps_status amplitude(const unsigned char* bits, double* out) = 0;
+  virtual mps_status get_site(int i, double* out, long long cap, int* dims3) = 0;
+  virtual mps_status lognorm(double* out) = 0;
+  virtual mps_status last_svals(double* out, int cap, int* count) = 0;
+  virtual mps_status sync() = 0;
+  virtual mps_status reset() = 0;
+  virtual mps_status profile(int on) = 0;
+  virtual mps_status stats(mps_stats_t* out) = 0;
+  virtual mps_status stats_reset() = 0;
+  int N = 0;
+  int d = 2;
+  int centre = 0;
+  std::vector<int> bonds;   // bonds[i] = left bond of site i; bonds[0] = bonds[N] = 1
+  std::vector<mps_trunc_record> log;
+  bool log_on = true;
+  int sticky = 0;
+  cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+template <class R>
+struct Engine final : mps_state {
+  using Z = cplx<R>;
+  mps_options opt{};
+  int sm_count = 1;
+  int chi_cap = kDefaultCap;
+  std::vector<int> cap;     // capacity of every bond
+  Z* arena = nullptr;
+  std::vector<Z*> site;
+  Z** site_dev = nullptr;
+  int* bonds_dev = nullptr;
+  Z *T = nullptr, *X = nullptr, *theta = nullptr, *Wacc = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+  Z *G = nullptr, *O = nullptr;
+  double *s_sorted = nullptr, *norms = nullptr;
+  int* perm = nullptr;
+  int c_max = 0;
+  int last_c = 0;
+  DevCtrl* ctrl = nullptr;
+  DevCtrl* hctrl = nullptr;
+  double2 *wdev = nullptr, *w2dev = nullptr, *work = nullptr, *outdev = nullptr, *hout = nullptr;
+  TcGemm* tc = nullptr;
+  // statistics
+  long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0;
+  double gemm_flops = 0.0, jac_ms = 0.0, gemm_ms = 0.0;
+  bool prof = false;
+  struct Timed { cudaEvent_t a, b; int kind; };
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> ev_pool;
+
+  ~Engine() override {
+    if (stream) cudaStreamSynchronize(stream);
+    void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
+                    ctrl, wdev, w2dev, work, outdev};
+    for (void* b : bufs) if (b) cudaFree(b);
+    if (hctrl) cudaFreeHost(hctrl);
+    if (hout) cudaFreeHost(hout);
+    if (tc) tc_destroy(tc);
+    for (auto& t : pending) { ev_pool.push_back(t.a); ev_pool.push_back(t.b); }
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+
+  cudaEvent_t ev_get() {
+    if (!ev_pool.empty()) { cudaEvent_t e = ev_pool.back(); ev_pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // start an event-timed region (kind 0 = Jacobi, 1 = contraction) on the handle's stream
+  int tbegin() {
+    if (!prof) return -1;
+    Timed t{ev_get(), ev_get(), 0};
+    cudaEventRecord(t.a, stream);
+    pending.push_back(t);
+    return (int)pending.size() - 1;
+  }
+  void tend(int id, int kind) {
+    if (id < 0) return;
+    pending[id].kind = kind;
+    cudaEventRecord(pending[id].b, stream);
+  }
+  // after a stream synchronisation: harvest the event durations
+  void harvest() {
+    for (auto& t : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) (t.kind == 0 ? jac_ms : gemm_ms) += ms;
+      ev_pool.push_back(t.a);
+      ev_pool.push_back(t.b);
+    }
+    pending.clear();
+  }
+  mps_status kl(cudaError_t e) { ++n_launch; return cu(e); }
+
+  template <class P> bool dalloc(P** p, size_t count) {
+    return cudaMalloc((void**)p, sizeof(P) * (count ? count : 1)) == cudaSuccess;
+  }
+
+  mps_status cu(cudaError_t e) {
+    if (e == cudaSuccess) return MPS_OK;
+    std::fprintf(stderr, "eamps: CUDA error: %s\n", cudaGetErrorString(e));
+    cudaGetLastError();
+    return MPS_ERR_CUDA;
+  }
+
+  mps_status init(int n, const mps_options& o, cudaStream_t st) {
+    N = n;
+    opt = o;
+    stream = st;
+    d = (o.kind == MPS_MIXED) ? 4 : 2;
+    log_on = o.log_truncations != 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MPS_ERR_CUDA;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    chi_cap = o.chi_max > 0 ? o.chi_max : kDefaultCap;
+    if (o.fixed_chi > 0) chi_cap = std::min(chi_cap, o.fixed_chi);
+    cap.assign(N + 1, 1);
+    for (int b = 1; b < N; ++b) {
+      const int e = std::min(b, N - b);
+      long long v = 1;
+      for (int i = 0; i < e && v < chi_cap; ++i) v *= d;
+      cap[b] = (int)std::min<long long>(v, chi_cap);
+    }
+    bonds.assign(N + 1, 1);
+    std::vector<size_t> off(N + 1);
+    size_t total = 0, site_max = 0, pair_max = 0;
+    for (int i = 0; i < N; ++i) {
+      off[i] = total;
+      const size_t sz = (size_t)cap[i] * d * cap[i + 1];
+      site_max = std::max(site_max, sz);
+      total += (sz + 31) & ~size_t(31);
+    }
+    for (int q = 0; q + 1 < N; ++q) {
+      const size_t m = (size_t)d * cap[q], nn = (size_t)d * cap[q + 2];
+      pair_max = std::max(pair_max, m * nn);
+      c_max = std::max<int>(c_max, (int)std::max(m, nn));
+    }
+    const size_t big = std::max(pair_max, site_max);
+    if (!dalloc(&arena, total) || !dalloc(&T, big) || !dalloc(&X, big) || !dalloc(&theta, big) ||
+        !dalloc(&Wacc, big) || !dalloc(&tmp, big) || !dalloc(&tmp2, big) || !dalloc(&G, 256) ||
+        !dalloc(&O, 256) || !dalloc(&s_sorted, c_max) || !dalloc(&norms, c_max) || !dalloc(&perm, c_max) ||
+        !dalloc(&site_dev, N) || !dalloc(&bonds_dev, N + 1) || !dalloc(&ctrl, 1) ||
+        !dalloc(&wdev, (size_t)N * d) || !dalloc(&w2dev, 16) || !dalloc(&work, (size_t)(2 + d) * (chi_cap + 8)) ||
+        !dalloc(&outdev, 4))
+      return MPS_ERR_OOM;
+    if (cudaMallocHost((void**)&hctrl, sizeof(DevCtrl)) != cudaSuccess) return MPS_ERR_OOM;
+    if (cudaMallocHost((void**)&hout, sizeof(double2) * 4) != cudaSuccess) return MPS_ERR_OOM;
+    site.resize(N);
+    for (int i = 0; i < N; ++i) site[i] = arena + off[i];
+    if (mps_status s = cu(cudaMemsetAsync(arena, 0, sizeof(Z) * total, stream))) return s;
+    // |0> (PURE) or vec(|0><0|) (MIXED, t = 0): entry [0, 0, 0] = 1 on every site
+    std::vector<Z> ones(1, mk<R>(1, 0));
+    for (int i = 0; i < N; ++i)
+      if (mps_status s = cu(cudaMemcpy(site[i], ones.data(), sizeof(Z), cudaMemcpyHostToDevice))) return s;
+    if (mps_status s = cu(cudaMemcpy(site_dev, site.data(), sizeof(Z*) * N, cudaMemcpyHostToDevice))) return s;
+    std::memset(hctrl, 0, sizeof(DevCtrl));
+    hctrl->product = 1.0;
+    hctrl->f_min = o.f_min;
+    hctrl->n_2q = o.n_2q;
+    hctrl->f0 = (o.f_min < 1.0 && o.n_2q > 0) ? std::pow(o.f_min, 1.0 / (double)o.n_2q) : 1.0;
+    hctrl->strategy = o.strategy;
+    hctrl->fixed_chi = o.fixed_chi;
+    hctrl->chi_max = chi_cap;
+    hctrl->mixed_fid = o.mixed_fid;
+    hctrl->kind = o.kind;
+    if (mps_status s = cu(cudaMemcpyAsync(ctrl, hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, stream))) return s;
+    if (mps_status s = cu(cudaStreamSynchronize(stream))) return s;
+    if (o.precision == MPS_TF32X3 && std::is_same<R, float>::value) {
+      tc = tc_create(big);
+      if (!tc) return MPS_ERR_OOM;
+    }
+    return MPS_OK;
+  }
+
+  // ------------------------------------------------------------- building blocks
+  mps_status gemm(int M, int Nn, int K, R alpha, const Z* A, long long a_rs, long long a_cs, int cA,
+                  const Z* B, long long b_rs, long long b_cs, int cB, Z* C, long long c_rs, long long c_cs) {
+    if (M <= 0 || Nn <= 0) return MPS_OK;
+    ++n_gemm;
+    gemm_flops += 8.0 * M * (double)Nn * K;
+    const int id = tbegin();
+    mps_status s;
+    if (tc) {
+      int launched = 0;
+      s = cu(tc_gemm(tc, M, Nn, K, (float)alpha, (const float2*)A, a_rs, a_cs, cA, (const float2*)B, b_rs, b_cs,
+                     cB, (float2*)C, c_rs, c_cs, stream, &launched));
+      n_launch += launched;
+    } else {
+      s = kl(cgemm_simt<R>(M, Nn, K, alpha, A, a_rs, a_cs, cA, B, b_rs, b_cs, cB, C, c_rs, c_cs, stream));
+    }
+    tend(id, 1);
+    return s;
+  }
+
+  // out[j*o_js + r*o_rs] = scale_j * op(src[col(j)*s_js + r*s_rs])
+  mps_status extract(Z* out, long long o_js, long long o_rs, int kout, int rows, const Z* src, long long s_js,
+                     long long s_rs, const int* pm, int conj, const double* sv, int wk) {
+    if (kout <= 0 || rows <= 0) return MPS_OK;
+    return kl(extract_columns<R>(out, o_js, o_rs, kout, rows, src, s_js, s_rs, pm, conj, sv, wk, ctrl, stream));
+  }
+
+  mps_status copy(Z* dst, const Z* src, size_t count) {
+    return cu(cudaMemcpyAsync(dst, src, sizeof(Z) * count, cudaMemcpyDeviceToDevice, stream));
+  }
+
+  mps_status run_jacobi(int l, int c, bool acc, Z* Xp, long long ldx) {
+    last_c = c;
+    if (acc)
+      if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
+    if (c <= 1) return MPS_OK;
+    JacobiPlan plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count);
+    const int fit = jacobi_max_ctas<R>(plan.smem);
+    if (fit <= 0) return MPS_ERR_CUDA;
+    if (plan.nb / 2 > fit) {
+      plan = jacobi_plan<R>(l, c, acc, sm_count, fit);
+      if (plan.nb / 2 > fit) return MPS_ERR_ARG;
+    }
+    ++n_jac;
+    const int id = tbegin();
+    mps_status s = kl(jacobi_launch<R>(plan, Xp, ldx, l, c, acc ? Wacc : nullptr, c, opt.max_sweeps, ctrl, stream));
+    tend(id, 0);
+    return s;
+  }
+
+  mps_status read_ctrl() {
+    if (mps_status s = cu(cudaMemcpyAsync(hctrl, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, stream))) return s;
+    if (mps_status s = cu(cudaStreamSynchronize(stream))) return s;
+    harvest();
+    sticky |= hctrl->status & (ST_TIMEOUT | ST_NONFINITE | ST_NOT_CONVERGED | ST_BAD_ARG);
+    return from_bits(sticky);
+  }
+
+  // ------------------------------------------------------------- centre moves
+  // Moving the orthogonality centre by one site replaces the QR step of the
+  // canonical form ("Canonicalization" section) by a one-sided Jacobi
+  // orthogonalisation: any isometry Q with C = Q R serves, and the bond
+  // becomes the rank bound min(rows, cols) exactly as with a reduced QR.
+  mps_status move_right(int c) {
+    const int m = bonds[c] * d, n = bonds[c + 1], n2 = d * bonds[c + 2];
+    Z* C = site[c];
+    Z* Nx = site[c + 1];
+    mps_status s;
+    if (n <= m) {
+      // X = C column-major; C W = Y; Q = Y/|Y| (m x n), R = Q^dagger C, A_{c+1} <- R A_{c+1}
+      if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;
+      if ((s = run_jacobi(m, n, false, X, m))) return s;
+      if ((s = kl(column_norms<R>(X, m, m, n, norms, stream)))) return s;
+      if ((s = extract(tmp, 1, n, n, m, X, m, 1, nullptr, 0, norms, 0))) return s;       // Q, row-major m x n
+      if ((s = gemm(n, n, m, R(1), tmp, 1, n, 1, C, n, 1, 0, tmp2, n, 1))) return s;       // R = Q^dagger C
+      if ((s = gemm(n, n2, n, R(1), tmp2, n, 1, 0, Nx, n2, 1, 0, T, n2, 1))) return s;     // R A_{c+1}
+      if ((s = copy(Nx, T, (size_t)n * n2))) return s;
+      if ((s = copy(C, tmp, (size_t)m * n))) return s;
+    } else {
+      // X = C^dagger (column i = conj of row i of C), accumulate W (m x m):
+      // C^dagger W = Y  ->  C = W Y^dagger: Q = W, R = Y^dagger
+      if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;
+      if ((s = run_jacobi(n, m, true, X, n))) return s;
+      if ((s = gemm(m, n2, n, R(1), X, n, 1, 1, Nx, n2, 1, 0, T, n2, 1))) return s;        // Y^dagger A_{c+1}
+      if ((s = copy(Nx, T, (size_t)m * n2))) return s;
+      if ((s = extract(C, 1, m, m, m, Wacc, m, 1, nullptr, 0, nullptr, 0))) return s;       // Q = W, row-major m x m
+      bonds[c + 1] = m;
+    }
+    centre = c + 1;
+    return MPS_OK;
+  }
+
+  mps_status move_left(int c) {
+    const int m = bonds[c], n = d * bonds[c + 1], m2 = bonds[c - 1] * d;
+    Z* C = site[c];
+    Z* Pv = site[c - 1];
+    mps_status s;
+    if (m <= n) {
+      // X = C^dagger; C^dagger W = Y -> C = (W S) Yn^dagger: Q' = Yn^dagger (m x n), L = C Q'^dagger
+      if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;
+      if ((s = run_jacobi(n, m, false, X, n))) return s;
+      if ((s = kl(column_norms<R>(X, n, n, m, norms, stream)))) return s;
+      if ((s = extract(tmp, n, 1, m, n, X, n, 1, nullptr, 1, norms, 0))) return s;        // Q' row-major m x n
+      if ((s = gemm(m, m, n, R(1), C, n, 1, 0, tmp, 1, n, 1, tmp2, m, 1))) return s;       // L = C Q'^dagger
+      if ((s = gemm(m2, m, m, R(1), Pv, m, 1, 0, tmp2, m, 1, 0, T, m, 1))) return s;       // A_{c-1} L
+      if ((s = copy(Pv, T, (size_t)m2 * m))) return s;
+      if ((s = copy(C, tmp, (size_t)m * n))) return s;
+    } else {
+      // X = C column-major, accumulate W (n x n): C W = Y -> C = Y W^dagger: Q' = W^dagger, L = Y
+      if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;
+      if ((s = run_jacobi(m, n, true, X, m))) return s;
+      if ((s = gemm(m2, n, m, R(1), Pv, m, 1, 0, X, 1, m, 0, T, n, 1))) return s;          // A_{c-1} Y
+      if ((s = copy(Pv, T, (size_t)m2 * n))) return s;
+      if ((s = extract(C, n, 1, n, n, Wacc, n, 1, nullptr, 1, nullptr, 0))) return s;      // W^dagger row-major
+      bonds[c] = n;
+    }
+    centre = c - 1;
+    return MPS_OK;
+  }
+
+  mps_status move_to(int to) {
+    while (centre < to)
+      if (mps_status s = move_right(centre)) return s;
+    while (centre > to)
+      if (mps_status s = move_left(centre)) return s;
+    return MPS_OK;
+  }
+
+  // ------------------------------------------------------------- operators
+  // Host copy of an operator lifted to the local index: PURE: as given; MIXED: a unitary U becomes
+  // the superoperator of U rho U^dagger, a superoperator is taken as given.
+  bool lift(const double* op, int op_dim, int nq, std::vector<double>& out) {
+    const int dloc = 1 << nq;                // qubit-space dimension
+    const int D = (d == 2) ? dloc : dloc * dloc;
+    if (d == 2) {
+      if (op_dim != dloc) return false;
+      out.assign(op, op + 2 * D * D);
+      return true;
+    }
+    if (op_dim == dloc) {
+      out.resize(2 * D * D);
+      superop_from_kraus_host(op, 1, nq, out.data());
+      return true;
+    }
+    if (op_dim != D) return false;
+    out.assign(op, op + 2 * D * D);
+    return true;
+  }
+
+  mps_status apply_1q(int q, const double* op, int op_dim) override {
+    if (sticky) return from_bits(sticky);
+    if (q < 0 || q >= N || !op) return MPS_ERR_ARG;
+    std::vector<double> g;
+    if (!lift(op, op_dim, 1, g)) return MPS_ERR_ARG;
+    mps_status s;
+    if ((s = kl(load_gate_param<R>(g.data(), d, G, stream)))) return s;
+    if (d == 4)
+      if ((s = move_to(q))) return s;
+    if ((s = kl(apply_local<R>(site[q], bonds[q], d, bonds[q + 1], G, stream)))) return s;
+    if (d == 4)
+      if ((s = kl(renormalise_site<R>(site[q], (long long)bonds[q] * d * bonds[q + 1], ctrl, stream)))) return s;
+    return MPS_OK;
+  }
+
+  // The hot path of the entanglement-aware algorithm for one two-qubit gate.
+  mps_status apply_2q(int q, const double* op, bool on_device, int op_dim, double target) override {
+    if (sticky) return from_bits(sticky);
+    if (q < 0 || q + 1 >= N || !op) return MPS_ERR_ARG;
+    const int D2 = d * d;
+    mps_status s;
+    if (on_device) {
+      if (!(op_dim == D2 && (d == 4 ? true : op_dim == 4))) return MPS_ERR_ARG;   // device operators: d^2 x d^2
+      if ((s = kl(load_gate_device<R>(op, D2, G, stream)))) return s;
+    } else {
+      std::vector<double> g;
+      if (!lift(op, op_dim, 2, g)) return MPS_ERR_ARG;
+      if ((s = kl(load_gate_param<R>(g.data(), D2, G, stream)))) return s;
+    }
+    // (a0) centre onto the pair: to q when it sits at or left of q (leaves at q+1), else to q+1
+    const bool right = centre <= q;
+    if ((s = move_to(right ? q : q + 1))) return s;
+    const int cl = bonds[q], chi = bonds[q + 1], cr = bonds[q + 2];
+    const int m = d * cl, n = d * cr;
+    // (a1) theta = A_q A_{q+1} (m x n as (cl, d, d, cr)), then the gate on the physical pair
+    if ((s = gemm(m, n, chi, R(1), site[q], chi, 1, 0, site[q + 1], n, 1, 0, T, n, 1))) return s;
+    // Jacobi on the short side; the orthonormal factor lands on the side the centre leaves
+    enum { R_COLS, R_ROWS_ACC, L_ROWS, L_COLS_ACC } mode;
+    if (right) mode = (n <= m) ? R_COLS : R_ROWS_ACC;
+    else mode = (m <= n) ? L_ROWS : L_COLS_ACC;
+    const bool cols = (mode == R_COLS || mode == L_COLS_ACC);     // X = theta (else theta^dagger)
+    const bool need_theta = (mode == R_COLS || mode == L_ROWS);
+    const int l = cols ? m : n, c = cols ? n : m;
+    if ((s = kl(gate_theta<R>(T, cl, d, cr, G, X, cols ? 0 : 1, need_theta ? theta : nullptr, stream)))) return s;
+    // (a2) SVD
+    const bool acc = (mode == R_ROWS_ACC || mode == L_COLS_ACC);
+    if ((s = run_jacobi(l, c, acc, X, l))) return s;
+    // (a3) selection and FP64 bookkeeping
+    if ((s = kl(select_bond<R>(X, l, l, c, ctrl, target, s_sorted, perm, stream)))) return s;
+    if ((s = read_ctrl())) return s;
+    const int k = hctrl->k;
+    const R inv_sqrt_wk = (R)(1.0 / std::sqrt(hctrl->Wk));
+    Z* Aq = site[q];
+    Z* Ap = site[q + 1];
+    // (a4) write-back: A_q (cl, d, k) row-major, A_{q+1} (k, d, cr) row-major
+    switch (mode) {
+      case R_COLS:   // U = Y/s; S V^dagger = U^dagger theta
+        if ((s = extract(Aq, 1, k, k, m, X, l, 1, perm, 0, s_sorted, 0))) return s;
+        if ((s = gemm(k, n, m, inv_sqrt_wk, Aq, 1, k, 1, theta, n, 1, 0, Ap, n, 1))) return s;
+        break;
+      case L_ROWS:   // V = Y/s (Y columns are conj rows of theta); U S = theta V
+        if ((s = extract(Ap, n, 1, k, n, X, l, 1, perm, 1, s_sorted, 0))) return s;
+        if ((s = gemm(m, k, n, inv_sqrt_wk, theta, n, 1, 0, Ap, 1, n, 1, Aq, k, 1))) return s;
+        break;
+      case R_ROWS_ACC:   // theta = W Y^dagger: U = W, S V^dagger = Y^dagger
+        if ((s = extract(Aq, 1, k, k, m, Wacc, c, 1, perm, 0, nullptr, 0))) return s;
+        if ((s = extract(Ap, n, 1, k, n, X, l, 1, perm, 1, nullptr, 1))) return s;
+        break;
+      case L_COLS_ACC:   // theta = Y W^dagger: U S = Y, V = W
+        if ((s = extract(Aq, 1, k, k, m, X, l, 1, perm, 0, nullptr, 1))) return s;
+        if ((s = extract(Ap, n, 1, k, n, Wacc, c, 1, perm, 1, nullptr, 0))) return s;
+        break;
+    }
+    bonds[q + 1] = k;
+    centre = right ? q + 1 : q;
+    ++n_gates;
+    if (log_on) {
+      mps_trunc_record r;
+      r.q = q; r.k = k; r.rank_bound = c; r.cap_hit = hctrl->cap_hit;
+      r.f = hctrl->f; r.f_t = hctrl->f_t; r.W = hctrl->W; r.W_k = hctrl->Wk;
+      log.push_back(r);
+    }
+    return hctrl->cap_hit ? MPS_WARN_CHI_CAP : MPS_OK;
+  }
+
+  mps_status fidelity(double* out) override {
+    mps_status s = read_ctrl();
+    *out = hctrl->product;
+    return s;
+  }
+
+  mps_status lognorm(double* out) override {
+    mps_status s = read_ctrl();
+    *out = hctrl->lognorm;
+    return s;
+  }
+
+  mps_status sync() override { return read_ctrl(); }
+
+  mps_status reset() override {
+    mps_status s;
+    if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+    harvest();
+    if ((s = kl(product_state<R>(site_dev, N, d, stream)))) return s;
+    std::fill(bonds.begin(), bonds.end(), 1);
+    centre = 0;
+    log.clear();
+    sticky = 0;
+    const double jf = hctrl->jac_flops;
+    const unsigned long long js = hctrl->jac_sweeps;
+    std::memset(hctrl, 0, sizeof(DevCtrl));
+    hctrl->product = 1.0;
+    hctrl->f_min = opt.f_min;
+    hctrl->n_2q = opt.n_2q;
+    hctrl->f0 = (opt.f_min < 1.0 && opt.n_2q > 0) ? std::pow(opt.f_min, 1.0 / (double)opt.n_2q) : 1.0;
+    hctrl->strategy = opt.strategy;
+    hctrl->fixed_chi = opt.fixed_chi;
+    hctrl->chi_max = chi_cap;
+    hctrl->mixed_fid = opt.mixed_fid;
+    hctrl->kind = opt.kind;
+    hctrl->jac_flops = jf;   // statistics survive a state reset
+    hctrl->jac_sweeps = js;
+    if ((s = cu(cudaMemcpyAsync(ctrl, hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, stream)))) return s;
+    return cu(cudaStreamSynchronize(stream));
+  }
+
+  mps_status profile(int on) override {
+    prof = on != 0;
+    return MPS_OK;
+  }
+
+  mps_status stats(mps_stats_t* out) override {
+    mps_status s = read_ctrl();
+    out->kernel_launches = n_launch;
+    out->jacobi_launches = n_jac;
+    out->jacobi_sweeps = (long long)hctrl->jac_sweeps;
+    out->jacobi_ms = jac_ms;
+    out->jacobi_flops = hctrl->jac_flops;
+    out->gemm_launches = n_gemm;
+    out->gemm_ms = gemm_ms;
+    out->gemm_flops = gemm_flops;
+    out->gates = n_gates;
+    return s;
+  }
+
+  mps_status stats_reset() override {
+    mps_status s;
+    if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+    harvest();
+    n_launch = n_jac = n_gemm = n_gates = 0;
+    gemm_flops = jac_ms = gemm_ms = 0.0;
+    const size_t off = offsetof(DevCtrl, jac_sweeps);
+    if ((s = cu(cudaMemsetAsync((char*)ctrl + off, 0, sizeof(DevCtrl) - off, stream)))) return s;
+    return cu(cudaStreamSynchronize(stream));
+  }
+
+  // v <- v * sum_t w_i[t] A_i[:, t, :] along the chain (optional two-site weight at q2)
+  mps_status chain(const std::vector<double2>& w, int q2, const double2* w2, double2* result) {
+    mps_status s;
+    if ((s = cu(cudaMemcpyAsync(bonds_dev, bonds.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, stream)))) return s;
+    if ((s = cu(cudaMemcpyAsync(wdev, w.data(), sizeof(double2) * w.size(), cudaMemcpyHostToDevice, stream)))) return s;
+    if (w2)
+      if ((s = cu(cudaMemcpyAsync(w2dev, w2, sizeof(double2) * 16, cudaMemcpyHostToDevice, stream)))) return s;
+    if ((s = kl(chain_contract<R>(N, (const Z* const*)site_dev, bonds_dev, d, wdev, q2, w2dev, work, chi_cap + 8,
+                                  outdev, stream))))
+      return s;
+    if ((s = cu(cudaMemcpyAsync(hout, outdev, sizeof(double2), cudaMemcpyDeviceToHost, stream)))) return s;
+    if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+    *result = hout[0];
+    return MPS_OK;
+  }
+
+  mps_status trace_stored(double2* tr) {
+    std::vector<double2> w((size_t)N * d, make_double2(0, 0));
+    for (int i = 0; i < N; ++i) { w[(size_t)i * d + 0] = make_double2(1, 0); w[(size_t)i * d + 3] = make_double2(1, 0); }
+    return chain(w, -1, nullptr, tr);
+  }
+
+  mps_status expect(int q, int support, const double* op, double* out) override {
+    if (sticky) return from_bits(sticky);
+    if (!op || !out || (support != 1 && support != 2) || q < 0 || q + support > N) return MPS_ERR_ARG;
+    mps_status s;
+    if (d == 2) {
+      const int D = support == 1 ? 2 : 4;
+      if ((s = kl(load_gate_param<R>(op, D, O, stream)))) return s;
+      if (support == 1) {
+        if ((s = move_to(q))) return s;
+        if ((s = kl(local_expect<R>(site[q], bonds[q], 2, bonds[q + 1], O, outdev, stream)))) return s;
+      } else {
+        if (centre > q + 1) { if ((s = move_to(q + 1))) return s; }
+        else if (centre < q) { if ((s = move_to(q))) return s; }
+        const int cl = bonds[q], chi = bonds[q + 1], cr = bonds[q + 2];
+        if ((s = gemm(2 * cl, 2 * cr, chi, R(1), site[q], chi, 1, 0, site[q + 1], 2 * cr, 1, 0, T, 2 * cr, 1))) return s;
+        if ((s = kl(local_expect<R>(T, cl, 4, cr, O, outdev, stream)))) return s;
+      }
+      if ((s = cu(cudaMemcpyAsync(hout, outdev, sizeof(double2), cudaMemcpyDeviceToHost, stream)))) return s;
+      if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+      out[0] = hout[0].x;
+      out[1] = hout[0].y;
+      return MPS_OK;
+    }
+    // MIXED: Tr(O rho) / Tr(rho), weights over t = 2 s + s': Tr(O rho) = sum O[s', s] rho[s, s']
+    std::vector<double2> w((size_t)N * d, make_double2(0, 0));
+    for (int i = 0; i < N; ++i) { w[(size_t)i * d + 0] = make_double2(1, 0); w[(size_t)i * d + 3] = make_double2(1, 0); }
+    double2 w2[16];
+    int q2 = -1;
+    if (support == 1) {
+      for (int sg = 0; sg < 2; ++sg)
+        for (int sp = 0; sp < 2; ++sp)
+          w[(size_t)q * d + 2 * sg + sp] = make_double2(op[2 * (sp * 2 + sg)], op[2 * (sp * 2 + sg) + 1]);
+    } else {
+      q2 = q;
+      for (int s1 = 0; s1 < 2; ++s1)
+        for (int s1p = 0; s1p < 2; ++s1p)
+          for (int s2 = 0; s2 < 2; ++s2)
+            for (int s2p = 0; s2p < 2; ++s2p) {
+              const int row = 2 * s1p + s2p, colx = 2 * s1 + s2;
+              w2[(2 * s1 + s1p) * 4 + (2 * s2 + s2p)] = make_double2(op[2 * (row * 4 + colx)], op[2 * (row * 4 + colx) + 1]);
+            }
+    }
+    double2 num, tr;
+    if ((s = chain(w, q2, q2 >= 0 ? w2 : nullptr, &num))) return s;
+    if ((s = trace_stored(&tr))) return s;
+    const double den = tr.x * tr.x + tr.y * tr.y;
+    out[0] = (num.x * tr.x + num.y * tr.y) / den;
+    out[1] = (num.y * tr.x - num.x * tr.y) / den;
+    return MPS_OK;
+  }
+
+  mps_status amplitude(const unsigned char* bits, double* out) override {
+    if (sticky) return from_bits(sticky);
+    if (!bits || !out) return MPS_ERR_ARG;
+    std::vector<double2> w((size_t)N * d, make_double2(0, 0));
+    for (int i = 0; i < N; ++i) {
+      if (bits[i] > 1) return MPS_ERR_ARG;
+      const int t = (d == 2) ? bits[i] : 3 * bits[i];
+      w[(size_t)i * d + t] = make_double2(1, 0);
+    }
+    double2 v;
+    mps_status s;
+    if ((s = chain(w, -1, nullptr, &v))) return s;
+    if (d == 4) {
+      double2 tr;
+      if ((s = trace_stored(&tr))) return s;
+      const double den = tr.x * tr.x + tr.y * tr.y;
+      const double2 r = make_double2((v.x * tr.x + v.y * tr.y) / den, (v.y * tr.x - v.x * tr.y) / den);
+      v = r;
+    }
+    out[0] = v.x;
+    out[1] = v.y;
+    return MPS_OK;
+  }
+
+  mps_status get_site(int i, double* out, long long capd, int* dims3) override {
+    if (i < 0 || i >= N || !out || !dims3) return MPS_ERR_ARG;
+    const long long count = (long long)bonds[i] * d * bonds[i + 1];
+    dims3[0] = bonds[i]; dims3[1] = d; dims3[2] = bonds[i + 1];
+    if (capd < 2 * count) return MPS_ERR_ARG;
+    mps_status s;
+    if ((s = kl(to_double<R>(site[i], (double2*)tmp, count, stream)))) return s;
+    if ((s = cu(cudaMemcpyAsync(out, tmp, sizeof(double2) * count, cudaMemcpyDeviceToHost, stream)))) return s;
+    return cu(cudaStreamSynchronize(stream));
+  }
+
+  mps_status last_svals(double* out, int capn, int* count) override {
+    if (!out || !count) return MPS_ERR_ARG;
+    const int nwr = std::min(capn, last_c);
+    *count = nwr;
+    if (nwr <= 0) return MPS_OK;
+    mps_status s;
+    if ((s = cu(cudaMemcpyAsync(out, s_sorted, sizeof(double) * nwr, cudaMemcpyDeviceToHost, stream)))) return s;
+    return cu(cudaStreamSynchronize(stream));
+  }
+};
+
+template <class R>
+mps_status make_engine(mps_handle* out, int n, const mps_options& o, cudaStream_t st) {
+  Engine<R>* e = new (std::nothrow) Engine<R>();
+  if (!e) return MPS_ERR_OOM;
+  mps_status s = e->init(n, o, st);
+  if (s != MPS_OK) { delete e; return s; }
+  *out = e;
+  return MPS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void mps_default_options(mps_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->kind = MPS_PURE;
+  o->f_min = 1.0;
+  o->n_2q = 0;
+  o->strategy = MPS_GLOBAL;
+  o->chi_max = 0;
+  o->fixed_chi = 0;
+  o->precision = MPS_TF32X3;
+  o->mixed_fid = MPS_KEPT_RATIO;
+  o->max_sweeps = 40;
+  o->log_truncations = 1;
+}
+
+const char* mps_status_string(mps_status s) {
+  switch (s) {
+    case MPS_OK: return "ok";
+    case MPS_ERR_ARG: return "invalid argument";
+    case MPS_ERR_NONADJACENT: return "gate on non-neighbouring qubits";
+    case MPS_ERR_OOM: return "out of memory";
+    case MPS_ERR_CUDA: return "CUDA error";
+    case MPS_ERR_NOT_CONVERGED: return "Jacobi SVD did not converge within max_sweeps";
+    case MPS_ERR_NONFINITE: return "non-finite singular value or weight";
+    case MPS_WARN_CHI_CAP: return "bond cap reached: fidelity target no longer guaranteed";
+    case MPS_ERR_TIMEOUT: return "device-side wait timed out";
+    case MPS_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+mps_status mps_create(mps_handle* out, int n_qubits, const mps_options* opt, void* cuda_stream) {
+  if (!out) return MPS_ERR_ARG;
+  *out = nullptr;
+  if (!opt || n_qubits < 2 || n_qubits > 100000) return MPS_ERR_ARG;
+  if (opt->kind != MPS_PURE && opt->kind != MPS_MIXED) return MPS_ERR_ARG;
+  if (!(opt->f_min > 0.0) || opt->strategy < 0 || opt->strategy > 2 || opt->chi_max < 0 || opt->fixed_chi < 0 ||
+      opt->precision < 0 || opt->precision > 2 || opt->mixed_fid < 0 || opt->mixed_fid > 1 || opt->max_sweeps < 1 ||
+      opt->n_2q < 0 || opt->chi_max > 4096)
+    return MPS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (opt->precision == MPS_FP64) return make_engine<double>(out, n_qubits, *opt, st);
+  return make_engine<float>(out, n_qubits, *opt, st);
+}
+
+mps_status mps_destroy(mps_handle h) {
+  delete h;
+  return MPS_OK;
+}
+
+mps_status mps_apply_1q(mps_handle h, int q, const double* op, int op_dim) {
+  if (!h) return MPS_ERR_ARG;
+  return h->apply_1q(q, op, op_dim);
+}
+
+mps_status mps_apply_2q(mps_handle h, int q, const double* op, int op_dim, double target) {
+  if (!h) return MPS_ERR_ARG;
+  return h->apply_2q(q, op, false, op_dim, target);
+}
+
+mps_status mps_apply_2q_device(mps_handle h, int q, const double* op_dev, int op_dim, double target) {
+  if (!h) return MPS_ERR_ARG;
+  return h->apply_2q(q, op_dev, true, op_dim, target);
+}
+
+mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
+                                    double target) {
+  if (!h || n_gates < 0 || (n_gates > 0 && (!qs || !ops_dev))) return MPS_ERR_ARG;
+  mps_status worst = MPS_OK;
+  for (int g = 0; g < n_gates; ++g) {
+    mps_status s = h->apply_2q(qs[g], ops_dev + (size_t)g * 2 * op_dim * op_dim, true, op_dim, target);
+    if (s == MPS_WARN_CHI_CAP) { worst = s; continue; }
+    if (s != MPS_OK) return s;
+  }
+  return worst;
+}
+
+mps_status mps_fidelity(mps_handle h, double* inferred) {
+  if (!h || !inferred) return MPS_ERR_ARG;
+  return h->fidelity(inferred);
+}
+
+mps_status mps_expect(mps_handle h, int q, int support, const double* op, double* out_re_im) {
+  if (!h) return MPS_ERR_ARG;
+  return h->expect(q, support, op, out_re_im);
+}
+
+mps_status mps_amplitude(mps_handle h, const unsigned char* bits, double* out_re_im) {
+  if (!h) return MPS_ERR_ARG;
+  return h->amplitude(bits, out_re_im);
+}
+
+mps_status mps_bond_dims(mps_handle h, int* out) {
+  if (!h || !out) return MPS_ERR_ARG;
+  for (int i = 0; i + 1 < h->N; ++i) out[i] = h->bonds[i + 1];
+  return MPS_OK;
+}
+
+mps_status mps_centre(mps_handle h, int* out) {
+  if (!h || !out) return MPS_ERR_ARG;
+  *out = h->centre;
+  return MPS_OK;
+}
+
+mps_status mps_get_site(mps_handle h, int i, double* out, long long cap, int* dims3) {
+  if (!h) return MPS_ERR_ARG;
+  return h->get_site(i, out, cap, dims3);
+}
+
+mps_status mps_lognorm(mps_handle h, double* out) {
+  if (!h || !out) return MPS_ERR_ARG;
+  return h->lognorm(out);
+}
+
+mps_status mps_last_singular_values(mps_handle h, double* out, int cap, int* count) {
+  if (!h) return MPS_ERR_ARG;
+  return h->last_svals(out, cap, count);
+}
+
+mps_status mps_truncation_log(mps_handle h, mps_trunc_record* out, int cap, int* count) {
+  if (!h || !count || (cap > 0 && !out)) return MPS_ERR_ARG;
+  const int n = std::min<int>(cap, (int)h->log.size());
+  for (int i = 0; i < n; ++i) out[i] = h->log[i];
+  *count = n;
+  return MPS_OK;
+}
+
+mps_status mps_sync(mps_handle h) {
+  if (!h) return MPS_ERR_ARG;
+  return h->sync();
+}
+
+mps_status mps_reset(mps_handle h) {
+  if (!h) return MPS_ERR_ARG;
+  return h->reset();
+}
+
+mps_status mps_profile(mps_handle h, int on) {
+  if (!h) return MPS_ERR_ARG;
+  return h->profile(on);
+}
+
+mps_status mps_stats(mps_handle h, mps_stats_t* out) {
+  if (!h || !out) return MPS_ERR_ARG;
+  return h->stats(out);
+}
+
+mps_status mps_stats_reset(mps_handle h) {
+  if (!h) return MPS_ERR_ARG;
+  return h->stats_reset();
+}
+
+mps_status mps_superop_from_kraus(const double* kraus, int n_kraus, int nq, double* out) {
+  if (!kraus || !out || n_kraus < 1 || (nq != 1 && nq != 2)) return MPS_ERR_ARG;
+  superop_from_kraus_host(kraus, n_kraus, nq, out);
+  return MPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,22 @@
+// Complex64 GEMM on the 5th-generation tensor cores (tcgen05, kind::tf32) with
+// the 3xTF32 split: each FP32 operand x = hi + lo (hi = x rounded to TF32),
+// A B ~ Ahi Bhi + Ahi Blo + Alo Bhi, accumulated in FP32 in tensor memory.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace eamps {
+
+struct TcGemm;
+
+// Workspace for operands of up to max_elems complex entries each.  nullptr on failure.
+TcGemm* tc_create(size_t max_elems);
+void tc_destroy(TcGemm* g);
+
+// C = alpha * op(A) * op(B) with the strided conventions of cgemm_simt (complex64).
+cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha,
+                    const float2* A, long long a_rs, long long a_cs, int conjA,
+                    const float2* B, long long b_rs, long long b_cs, int conjB,
+                    float2* C, long long c_rs, long long c_cs, cudaStream_t st, int* launched);
+
+}  // namespace eamps

@@ -1,0 +1,102 @@
+// Launchers of the EA-MPS device kernels (host-callable, templated on the real type).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace eamps {
+
+// ------------------------------------------------------------ Jacobi SVD
+// One-sided Jacobi on the c columns (length l, column j at X + j*ldx) of X:
+// on return X V = Y (mutually orthogonal columns, |Y_j| = singular value j,
+// unordered).  If W != nullptr the rotations are also applied to the c x c
+// matrix W (column j at W + j*ldw), which must hold the identity on entry, so
+// that W = V.  Cooperative launch; status bits and sweep count go to ctrl.
+struct JacobiPlan {
+  int w = 1;       // columns per block
+  int nb = 2;      // number of blocks (even); CTAs = nb / 2
+  size_t smem = 0; // dynamic shared memory per CTA
+};
+template <class R>
+JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas);
+template <class R>
+cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int l, int c,
+                          cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cudaStream_t st);
+template <class R> int jacobi_max_ctas(size_t smem);
+
+// ------------------------------------------------------------ CUDA-core GEMM
+// C = alpha * op(A) * op(B); op(A)[i,k] = A[i*a_rs + k*a_cs] (conjugated if conjA).
+template <class R>
+cudaError_t cgemm_simt(int M, int N, int K, R alpha,
+                       const cplx<R>* A, long long a_rs, long long a_cs, int conjA,
+                       const cplx<R>* B, long long b_rs, long long b_cs, int conjB,
+                       cplx<R>* C, long long c_rs, long long c_cs, cudaStream_t st);
+
+// ------------------------------------------------------------ small kernels
+// gate (d2 x d2, row-major complex doubles) -> device buffer in precision R
+template <class R>
+cudaError_t load_gate_param(const double* host_op, int d2, cplx<R>* dst, cudaStream_t st);
+template <class R>
+cudaError_t load_gate_device(const double* dev_op, int d2, cplx<R>* dst, cudaStream_t st);
+
+// theta[(a s1),(s2 b)] = sum_{t1 t2} G[(s1 s2),(t1 t2)] T[a,t1,t2,b];  writes X (xmode 0: theta
+// column-major, ld = m; xmode 1: conj(theta) row-major = theta^dagger column-major, ld = n) and
+// optionally theta row-major.
+template <class R>
+cudaError_t gate_theta(const cplx<R>* T, int chiL, int d, int chiR, const cplx<R>* G,
+                       cplx<R>* X, int xmode, cplx<R>* theta, cudaStream_t st);
+
+// Sort the column norms of Y (FP64) in decreasing order, choose the bond (entanglement-aware rule,
+// fixed chi or cap), update the FP64 product / schedule / log-norm in ctrl, and write the sorted
+// singular values and the permutation.  c <= 8192.
+template <class R>
+cudaError_t select_bond(const cplx<R>* Y, long long ldy, int l, int c, DevCtrl* ctrl, double target,
+                        double* s_sorted, int* perm, cudaStream_t st);
+
+// FP64 norms of the c columns (length l) of Y.
+template <class R>
+cudaError_t column_norms(const cplx<R>* Y, long long ldy, int l, int c, double* norms, cudaStream_t st);
+
+// out[j*o_js + r*o_rs] = scale_j * op(src[col(j)*s_js + r*s_rs]) for j < kout, r < rows, where
+// col(j) = perm ? perm[j] : j, op = conj if conj, scale_j = (svals ? 1/svals[j] (0 if svals[j]==0) : 1)
+// * (wk_scale ? 1/sqrt(ctrl->Wk) : 1).
+template <class R>
+cudaError_t extract_columns(cplx<R>* out, long long o_js, long long o_rs, int kout, int rows,
+                            const cplx<R>* src, long long s_js, long long s_rs, const int* perm, int conj,
+                            const double* svals, int wk_scale, const DevCtrl* ctrl, cudaStream_t st);
+
+// Identity into a c x c column-major matrix (ld).
+template <class R>
+cudaError_t set_identity(cplx<R>* W, long long ld, int c, cudaStream_t st);
+
+// A'[a,s,b] = sum_t G[s,t] A[a,t,b] in place, site (chiL, d, chiR).
+template <class R>
+cudaError_t apply_local(cplx<R>* A, int chiL, int d, int chiR, const cplx<R>* G, cudaStream_t st);
+
+// Normalise a site to unit Frobenius norm (FP64), lognorm += log(norm).
+template <class R>
+cudaError_t renormalise_site(cplx<R>* A, long long count, DevCtrl* ctrl, cudaStream_t st);
+
+// sum_{a,b,s,t} conj(T[a,s,b]) O[s,t] T[a,t,b] (FP64) into *out (double2, device); O is D x D.
+template <class R>
+cudaError_t local_expect(const cplx<R>* T, int chiL, int D, int chiR, const cplx<R>* O, double2* out,
+                         cudaStream_t st);
+
+// Transfer contraction along the chain: v <- v * sum_t w_i[t] A_i[:,t,:], with an optional
+// two-site weight w2 (d x d, indices (t_q, t_q+1)) replacing the weights of sites q, q+1.
+// sites: device array of N site pointers; bonds: device, N+1 entries.
+template <class R>
+cudaError_t chain_contract(int N, const cplx<R>* const* sites, const int* bonds, int d,
+                           const double2* w, int q2, const double2* w2, double2* work, int max_chi,
+                           double2* out, cudaStream_t st);
+
+// Product state |0...0> (or vec(|0..0><0..0|)): site i = (1, d, 1), entry 0 = 1.
+template <class R>
+cudaError_t product_state(cplx<R>* const* sites, int N, int d, cudaStream_t st);
+
+// Convert a site to complex128.
+template <class R>
+cudaError_t to_double(const cplx<R>* src, double2* dst, long long count, cudaStream_t st);
+
+}  // namespace eamps

@@ -1,0 +1,67 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared
+symbol, and its host-side helpers agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+import workloads as W
+from oracle import superop as SO
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "eamps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mps_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("mps_create", "mps_destroy", "mps_apply_1q", "mps_apply_2q", "mps_fidelity", "mps_expect",
+              "mps_amplitude", "mps_bond_dims"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2307_16870_gb300 as E
+    lib = E.load()
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_defaults():
+    import paper_2307_16870_gb300 as E
+    assert E.mps_status_string(0) == "ok"
+    assert "cap" in E.mps_status_string(7)
+    o = E.mps_default_options()
+    assert o.kind == E.PURE and o.strategy == E.GLOBAL and o.precision == E.TF32X3 and o.max_sweeps == 40
+
+
+def test_options_struct_layout_matches_header():
+    import paper_2307_16870_gb300 as E
+    # int, double, long long, 7 ints -> 4 + 4(pad) + 8 + 8 + 7*4 = 52 -> 56 with tail padding
+    assert ctypes.sizeof(E.MpsOptions) == 56
+    assert ctypes.sizeof(E.TruncRecord) == 48
+
+
+def test_superop_helper_matches_oracle():
+    import paper_2307_16870_gb300 as E
+    ks = [W.haar_unitary(4, 7, 0) @ k for k in W.depolarizing_2q_kraus(0.05)]
+    assert np.abs(E.mps_superop_from_kraus(ks, 2) - SO.from_kraus(ks, 2)).max() < 1e-14
+    ad = W.amplitude_damping_kraus(0.2)
+    assert np.abs(E.mps_superop_from_kraus(ad, 1) - SO.from_kraus(ad, 1)).max() < 1e-15
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu():
+    import paper_2307_16870_gb300 as E
+    lib = E.load()
+    h = ctypes.c_void_p()
+    o = E.mps_default_options()
+    assert lib.mps_create(ctypes.byref(h), 1, ctypes.byref(o), None) == 1      # N < 2
+    o.kind = 5
+    assert lib.mps_create(ctypes.byref(h), 4, ctypes.byref(o), None) == 1
+    assert h.value is None
+    assert lib.mps_destroy(None) == 0
