@@ -169,6 +169,20 @@ mps_status mps_centre(mps_handle h, int* out);
  * shape.  Errors: MPS_ERR_ARG if cap (in doubles) is too small. */
 mps_status mps_get_site(mps_handle h, int i, double* out, long long cap, int* dims3);
 
+/* Load site tensor i from the host: complex128 (2*chi_L*d*chi_R doubles,
+ * row-major (chi_L, d, chi_R)), dims3 = {chi_L, d, chi_R}; converted to the
+ * handle's working precision.  Sets bonds i and i+1 to chi_L and chi_R.  The
+ * caller loads every site it changes with consistent bonds and then declares
+ * the orthogonality centre with mps_set_centre; the state must be in
+ * canonical form around that centre ("Canonicalization" section) for the
+ * truncation fidelities to hold.  Together with mps_get_site this saves and
+ * restores a state.  Errors: MPS_ERR_ARG (index, d, bonds above the handle's
+ * capacity min(cap, d^min(i, N-i)) or zero). */
+mps_status mps_set_site(mps_handle h, int i, const double* data, const int* dims3);
+
+/* Declare site c the orthogonality centre (no computation). */
+mps_status mps_set_centre(mps_handle h, int c);
+
 /* FP64 log of the norm factor of an MPO (rho = exp(lognorm) * stored rho). */
 mps_status mps_lognorm(mps_handle h, double* out);
 
@@ -208,6 +222,22 @@ typedef struct {
 mps_status mps_profile(mps_handle h, int on);
 mps_status mps_stats(mps_handle h, mps_stats_t* out);
 mps_status mps_stats_reset(mps_handle h);
+
+/* Complex64 GEMM on device buffers with the library's contraction kernels:
+ * C = alpha * op(A) * op(B), op(A)[i,k] = A[i*a_rs + k*a_cs] (conjugated if
+ * conjA), likewise for B; C[i,j] at C + i*c_rs + j*c_cs.  A, B, C: DEVICE
+ * float2 (interleaved complex64).  precision = MPS_TF32X3 (tcgen05 tensor
+ * cores, 3xTF32 split, FP32 accumulation) or MPS_FP32 (CUDA cores).  This is
+ * the contraction used for theta (the product of the two site tensors,
+ * "Truncation fidelity" section); it is exported so that callers and tests
+ * can run it alone.  Allocates (and frees) its packing workspace per call;
+ * ordered on cuda_stream and synchronised before return.
+ * Errors: MPS_ERR_ARG (sizes, precision), MPS_ERR_OOM, MPS_ERR_CUDA,
+ * MPS_ERR_TIMEOUT. */
+mps_status mps_cgemm_c64(int precision, int M, int N, int K, float alpha,
+                         const void* A, long long a_rs, long long a_cs, int conjA,
+                         const void* B, long long b_rs, long long b_cs, int conjB,
+                         void* C, long long c_rs, long long c_cs, void* cuda_stream);
 
 /* Host helper: the superoperator of the channel {K} (n_kraus operators of
  * dimension 2^nq, host, 2*4^nq doubles each, concatenated) in the library's

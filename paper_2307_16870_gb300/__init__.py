@@ -25,7 +25,8 @@ __all__ = [
     "mps_apply_2q_device", "mps_apply_circuit_device", "mps_fidelity", "mps_expect", "mps_amplitude",
     "mps_bond_dims", "mps_centre", "mps_get_site", "mps_lognorm", "mps_last_singular_values",
     "mps_truncation_log", "mps_sync", "mps_superop_from_kraus", "mps_status_string",
-    "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats",
+    "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
+    "mps_set_site", "mps_set_centre",
 ]
 
 PURE, MIXED = 0, 1
@@ -36,7 +37,7 @@ KEPT_RATIO, WANG_SQRT = 0, 1
 OK, WARN_CHI_CAP = 0, 7
 
 # The tensor-core (tcgen05) contraction path of precision TF32X3.
-TC_AVAILABLE = False
+TC_AVAILABLE = True
 
 
 class MpsOptions(C.Structure):
@@ -93,11 +94,16 @@ def load(path: str | None = None):
         "mps_centre": (C.c_int, [H, C.POINTER(C.c_int)]),
         "mps_get_site": (C.c_int, [H, C.c_int, D, C.c_longlong, C.POINTER(C.c_int)]),
         "mps_lognorm": (C.c_int, [H, D]),
+        "mps_set_site": (C.c_int, [H, C.c_int, D, C.POINTER(C.c_int)]),
+        "mps_set_centre": (C.c_int, [H, C.c_int]),
         "mps_last_singular_values": (C.c_int, [H, D, C.c_int, C.POINTER(C.c_int)]),
         "mps_truncation_log": (C.c_int, [H, C.POINTER(TruncRecord), C.c_int, C.POINTER(C.c_int)]),
         "mps_sync": (C.c_int, [H]),
         "mps_superop_from_kraus": (C.c_int, [D, C.c_int, C.c_int, D]),
         "mps_reset": (C.c_int, [H]),
+        "mps_cgemm_c64": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_longlong,
+                                    C.c_longlong, C.c_int, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int,
+                                    C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p]),
         "mps_profile": (C.c_int, [H, C.c_int]),
         "mps_stats": (C.c_int, [H, C.POINTER(MpsStats)]),
         "mps_stats_reset": (C.c_int, [H]),
@@ -215,6 +221,19 @@ def mps_get_site(h: int, i: int, max_elems: int) -> np.ndarray:
     return buf[: 2 * n].view(np.complex128).reshape(dims[0], dims[1], dims[2]).copy()
 
 
+def mps_set_site(h: int, i: int, tensor) -> int:
+    t = np.ascontiguousarray(np.asarray(tensor, dtype=np.complex128))
+    if t.ndim != 3:
+        raise ValueError("site tensor must be (chi_L, d, chi_R)")
+    dims = (C.c_int * 3)(*t.shape)
+    return _check(load().mps_set_site(C.c_void_p(h), int(i), _dptr(t.view(np.float64).reshape(-1)), dims),
+                  "mps_set_site")
+
+
+def mps_set_centre(h: int, c: int) -> int:
+    return _check(load().mps_set_centre(C.c_void_p(h), int(c)), "mps_set_centre")
+
+
 def mps_lognorm(h: int) -> float:
     v = C.c_double()
     _check(load().mps_lognorm(C.c_void_p(h), C.byref(v)), "mps_lognorm")
@@ -256,6 +275,14 @@ def mps_stats(h: int) -> dict:
 
 def mps_stats_reset(h: int) -> int:
     return _check(load().mps_stats_reset(C.c_void_p(h)), "mps_stats_reset")
+
+
+def mps_cgemm_c64(precision: int, M: int, N: int, K: int, alpha: float, A: int, a_rs: int, a_cs: int, conjA: bool,
+                  B: int, b_rs: int, b_cs: int, conjB: bool, Cp: int, c_rs: int, c_cs: int, stream: int = 0) -> int:
+    """C = alpha op(A) op(B) on device complex64 buffers (pointers as ints)."""
+    return _check(load().mps_cgemm_c64(int(precision), M, N, K, float(alpha), C.c_void_p(A), a_rs, a_cs, int(conjA),
+                                       C.c_void_p(B), b_rs, b_cs, int(conjB), C.c_void_p(Cp), c_rs, c_cs,
+                                       C.c_void_p(stream or None)), "mps_cgemm_c64")
 
 
 def mps_superop_from_kraus(kraus: list, nq: int) -> np.ndarray:
@@ -326,6 +353,12 @@ class MPS:
 
     def lognorm(self):
         return mps_lognorm(self.h)
+
+    def load_sites(self, sites, centre: int):
+        """Load every site tensor (list of (chi_L, d, chi_R) arrays) and declare the centre."""
+        for i, a in enumerate(sites):
+            mps_set_site(self.h, i, a)
+        mps_set_centre(self.h, centre)
 
     def last_singular_values(self):
         return mps_last_singular_values(self.h)

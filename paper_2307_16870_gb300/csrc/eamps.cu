@@ -67,6 +67,7 @@ struct mps_state {
   virtual mps_status expect(int q, int support, const double* op, double* out) = 0;
   virtual mps_status amplitude(const unsigned char* bits, double* out) = 0;
   virtual mps_status get_site(int i, double* out, long long cap, int* dims3) = 0;
+  virtual mps_status set_site(int i, const double* data, const int* dims3) = 0;
   virtual mps_status lognorm(double* out) = 0;
   virtual mps_status last_svals(double* out, int cap, int* count) = 0;
   virtual mps_status sync() = 0;
@@ -106,6 +107,8 @@ struct Engine final : mps_state {
   DevCtrl* ctrl = nullptr;
   DevCtrl* hctrl = nullptr;
   double2 *wdev = nullptr, *w2dev = nullptr, *work = nullptr, *outdev = nullptr, *hout = nullptr;
+  double2* stage = nullptr;   // complex128 staging of one site (mps_get_site)
+  size_t site_cap = 0;
   TcGemm* tc = nullptr;
   // statistics
   long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0;
@@ -118,7 +121,7 @@ struct Engine final : mps_state {
   ~Engine() override {
     if (stream) cudaStreamSynchronize(stream);
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
-                    ctrl, wdev, w2dev, work, outdev};
+                    ctrl, wdev, w2dev, work, outdev, stage};
     for (void* b : bufs) if (b) cudaFree(b);
     if (hctrl) cudaFreeHost(hctrl);
     if (hout) cudaFreeHost(hout);
@@ -207,8 +210,9 @@ struct Engine final : mps_state {
         !dalloc(&O, 256) || !dalloc(&s_sorted, c_max) || !dalloc(&norms, c_max) || !dalloc(&perm, c_max) ||
         !dalloc(&site_dev, N) || !dalloc(&bonds_dev, N + 1) || !dalloc(&ctrl, 1) ||
         !dalloc(&wdev, (size_t)N * d) || !dalloc(&w2dev, 16) || !dalloc(&work, (size_t)(2 + d) * (chi_cap + 8)) ||
-        !dalloc(&outdev, 4))
+        !dalloc(&outdev, 4) || !dalloc(&stage, site_max))
       return MPS_ERR_OOM;
+    site_cap = site_max;
     if (cudaMallocHost((void**)&hctrl, sizeof(DevCtrl)) != cudaSuccess) return MPS_ERR_OOM;
     if (cudaMallocHost((void**)&hout, sizeof(double2) * 4) != cudaSuccess) return MPS_ERR_OOM;
     site.resize(N);
@@ -246,10 +250,10 @@ struct Engine final : mps_state {
     gemm_flops += 8.0 * M * (double)Nn * K;
     const int id = tbegin();
     mps_status s;
-    if (tc) {
+    if (tc && K >= 8 && (long long)M * Nn * K >= 32768LL && tc_fits(tc, M, Nn, K)) {
       int launched = 0;
       s = cu(tc_gemm(tc, M, Nn, K, (float)alpha, (const float2*)A, a_rs, a_cs, cA, (const float2*)B, b_rs, b_cs,
-                     cB, (float2*)C, c_rs, c_cs, stream, &launched));
+                     cB, (float2*)C, c_rs, c_cs, stream, &launched, &ctrl->status));
       n_launch += launched;
     } else {
       s = kl(cgemm_simt<R>(M, Nn, K, alpha, A, a_rs, a_cs, cA, B, b_rs, b_cs, cB, C, c_rs, c_cs, stream));
@@ -644,11 +648,27 @@ struct Engine final : mps_state {
     if (i < 0 || i >= N || !out || !dims3) return MPS_ERR_ARG;
     const long long count = (long long)bonds[i] * d * bonds[i + 1];
     dims3[0] = bonds[i]; dims3[1] = d; dims3[2] = bonds[i + 1];
-    if (capd < 2 * count) return MPS_ERR_ARG;
+    if (capd < 2 * count || (size_t)count > site_cap) return MPS_ERR_ARG;
     mps_status s;
-    if ((s = kl(to_double<R>(site[i], (double2*)tmp, count, stream)))) return s;
-    if ((s = cu(cudaMemcpyAsync(out, tmp, sizeof(double2) * count, cudaMemcpyDeviceToHost, stream)))) return s;
+    if ((s = kl(to_double<R>(site[i], stage, count, stream)))) return s;
+    if ((s = cu(cudaMemcpyAsync(out, stage, sizeof(double2) * count, cudaMemcpyDeviceToHost, stream)))) return s;
     return cu(cudaStreamSynchronize(stream));
+  }
+
+  mps_status set_site(int i, const double* data, const int* dims3) override {
+    if (sticky) return from_bits(sticky);
+    if (i < 0 || i >= N || !data || !dims3) return MPS_ERR_ARG;
+    const int cl = dims3[0], dd = dims3[1], cr = dims3[2];
+    if (dd != d || cl < 1 || cr < 1 || cl > cap[i] || cr > cap[i + 1]) return MPS_ERR_ARG;
+    if ((i == 0 && cl != 1) || (i == N - 1 && cr != 1)) return MPS_ERR_ARG;
+    const long long count = (long long)cl * d * cr;
+    mps_status s;
+    if ((s = cu(cudaMemcpyAsync(stage, data, sizeof(double2) * count, cudaMemcpyHostToDevice, stream)))) return s;
+    if ((s = kl(from_double<R>(stage, site[i], count, stream)))) return s;
+    if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+    bonds[i] = cl;
+    bonds[i + 1] = cr;
+    return MPS_OK;
   }
 
   mps_status last_svals(double* out, int capn, int* count) override {
@@ -786,6 +806,17 @@ mps_status mps_get_site(mps_handle h, int i, double* out, long long cap, int* di
   return h->get_site(i, out, cap, dims3);
 }
 
+mps_status mps_set_site(mps_handle h, int i, const double* data, const int* dims3) {
+  if (!h) return MPS_ERR_ARG;
+  return h->set_site(i, data, dims3);
+}
+
+mps_status mps_set_centre(mps_handle h, int c) {
+  if (!h || c < 0 || c >= h->N) return MPS_ERR_ARG;
+  h->centre = c;
+  return MPS_OK;
+}
+
 mps_status mps_lognorm(mps_handle h, double* out) {
   if (!h || !out) return MPS_ERR_ARG;
   return h->lognorm(out);
@@ -827,6 +858,37 @@ mps_status mps_stats(mps_handle h, mps_stats_t* out) {
 mps_status mps_stats_reset(mps_handle h) {
   if (!h) return MPS_ERR_ARG;
   return h->stats_reset();
+}
+
+mps_status mps_cgemm_c64(int precision, int M, int N, int K, float alpha, const void* A, long long a_rs,
+                         long long a_cs, int conjA, const void* B, long long b_rs, long long b_cs, int conjB, void* C,
+                         long long c_rs, long long c_cs, void* cuda_stream) {
+  if (M < 0 || N < 0 || K < 0 || !A || !B || !C) return MPS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e;
+  if (precision == MPS_FP32) {
+    e = cgemm_simt<float>(M, N, K, alpha, (const float2*)A, a_rs, a_cs, conjA, (const float2*)B, b_rs, b_cs, conjB,
+                          (float2*)C, c_rs, c_cs, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MPS_OK : MPS_ERR_CUDA;
+  }
+  if (precision != MPS_TF32X3) return MPS_ERR_ARG;
+  const size_t need = (size_t)std::max<long long>((long long)M * (K + 16), (long long)N * (K + 16));
+  TcGemm* g = tc_create(need);
+  if (!g) return MPS_ERR_OOM;
+  int* status = nullptr;
+  if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) { tc_destroy(g); return MPS_ERR_OOM; }
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  int launched = 0;
+  e = tc_gemm(g, M, N, K, alpha, (const float2*)A, a_rs, a_cs, conjA, (const float2*)B, b_rs, b_cs, conjB,
+              (float2*)C, c_rs, c_cs, st, &launched, status);
+  int hs = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(status);
+  tc_destroy(g);
+  if (e != cudaSuccess) { std::fprintf(stderr, "eamps: CUDA error: %s\n", cudaGetErrorString(e)); return MPS_ERR_CUDA; }
+  return (hs & ST_TIMEOUT) ? MPS_ERR_TIMEOUT : MPS_OK;
 }
 
 mps_status mps_superop_from_kraus(const double* kraus, int n_kraus, int nq, double* out) {

@@ -1,15 +1,354 @@
-// Tensor-core complex GEMM (tcgen05): interface placeholder until the kernel lands.
+// Complex64 GEMM on the tcgen05 tensor cores (sm_103a), 3xTF32 split.
+//
+// The complex product C = op(A) op(B) (M x K times K x N) is one real GEMM on
+// interleaved operands: A' (M x 2K) holds (Re, Im) pairs of each row of
+// op(A); B' (2N x 2K, K-major) holds for complex column j the two real rows
+//   2j  : ( Re b, -Im b ) per k     -> real part of c_ij
+//   2j+1: ( Im b,  Re b ) per k     -> imaginary part of c_ij
+// so that D = A' B'^T (M x 2N) interleaves (Re, Im) of C.  Each FP32 operand
+// is split x = hi + lo with hi = x rounded to TF32 and lo = x - hi (exact),
+// and D = Ahi Bhi + Ahi Blo + Alo Bhi accumulates in FP32 in tensor memory:
+// FP32-level accuracy from kind::tf32 MMAs.
+//
+// Kernel: one CTA per 128 x 128 tile of D, four warps.  Warp 0 (one lane)
+// drives TMA loads of 32-wide K blocks (128-byte swizzled, K-major) into a
+// three-stage shared-memory ring; warp 1 (one lane) issues 12 tcgen05.mma per
+// block (3 products x 4 K-steps of 8) into a 128-column TMEM accumulator and
+// releases each stage with tcgen05.commit; all four warps then read the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31) and store
+// complex results with the caller's strides and scale.  Every mbarrier wait
+// is bounded; a timeout sets the status bit and the CTA drains and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "common.cuh"
 #include "gemm_tc.h"
 
 namespace eamps {
 
-struct TcGemm { int unused; };
+namespace {
 
-TcGemm* tc_create(size_t) { return nullptr; }
-void tc_destroy(TcGemm*) {}
-cudaError_t tc_gemm(TcGemm*, int, int, int, float, const float2*, long long, long long, int, const float2*, long long,
-                    long long, int, float2*, long long, long long, cudaStream_t, int*) {
-  return cudaErrorNotSupported;
+constexpr int BM = 128, BN = 128, BKR = 32;      // BKR: real K elements per block (128 bytes)
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BKR * 4;          // 16 KB, same for A and B tiles (BN == BM)
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr long long kWaitLimit = 40000000LL;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; on timeout sets ST_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i > 64) __nanosleep(20);
+  }
+  atomicOr(status, ST_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(su32(dst)), "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (the layout TMA writes with SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;              // descriptor version of this architecture
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh,
+                                                         const __grid_constant__ CUtensorMap mAl,
+                                                         const __grid_constant__ CUtensorMap mBh,
+                                                         const __grid_constant__ CUtensorMap mBl,
+                                                         int M, int N, int nkb, float alpha,
+                                                         float2* __restrict__ C, long long c_rs, long long c_cs,
+                                                         int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;   // real columns of D
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    mbar_init(&done_bar, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base_s)),
+                 "r"(128u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  constexpr uint32_t IDESC = idesc_tf32(BM, BN);
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1, status)) { abort_s = 1; break; }
+      unsigned char* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      tma_load_2d(st + 0 * TILE_BYTES, &mAh, &full_bar[s], kb * BKR, m0);
+      tma_load_2d(st + 1 * TILE_BYTES, &mAl, &full_bar[s], kb * BKR, m0);
+      tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full_bar[s], kb * BKR, n0);
+      tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full_bar[s], kb * BKR, n0);
+      issued = kb + 1;
+    }
+    // drain: every issued stage must have landed before the CTA may exit
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+      mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, status);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, status)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t base = su32(smem + s * STAGE_BYTES);
+      const uint64_t dAh = sdesc(base), dAl = sdesc(base + TILE_BYTES);
+      const uint64_t dBh = sdesc(base + 2 * TILE_BYTES), dBl = sdesc(base + 3 * TILE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BKR / 8; ++kk) {
+        const uint64_t adv = (uint64_t)((kk * 32) >> 4);   // 8 TF32 = 32 bytes along K
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, dAl + adv, dBh + adv, IDESC, acc);
+        mma_tf32(tmem, dAh + adv, dBl + adv, IDESC, 1u);
+        mma_tf32(tmem, dAh + adv, dBh + adv, IDESC, 1u);
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    if (!ok) abort_s = 1;
+    mma_commit(&done_bar);   // arrives once every MMA issued above has completed
+  }
+  __syncthreads();
+  // ---------------- epilogue (all four warps)
+  const bool done = mbar_wait(&done_bar, 0, status);
+  tc_fence_after();
+  if (done && !abort_s) {
+    const int row = m0 + warp * 32 + lane;
+    for (int ch = 0; ch < BN / 32; ++ch) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+      if (row < M) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = (n0 + ch * 32) / 2 + c;
+          if (j < N) {
+            float2 z;
+            z.x = alpha * __uint_as_float(v[2 * c]);
+            z.y = alpha * __uint_as_float(v[2 * c + 1]);
+            C[(long long)row * c_rs + (long long)j * c_cs] = z;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+}
+
+// Pack op(A) (M x K complex) into interleaved real rows, split hi/lo: ld = kpad reals.
+__global__ void pack_a_kernel(const float2* __restrict__ A, long long a_rs, long long a_cs, int conj, int M, int K,
+                              int kpad, float* __restrict__ hi, float* __restrict__ lo) {
+  const long long total = (long long)M * (kpad / 2);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / (kpad / 2)), k = (int)(e % (kpad / 2));
+    float2 v = make_float2(0.f, 0.f);
+    if (k < K) { v = A[i * a_rs + k * a_cs]; if (conj) v.y = -v.y; }
+    float h0, h1;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(h0) : "f"(v.x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(h1) : "f"(v.y));
+    const long long o = (long long)i * kpad + 2 * k;
+    reinterpret_cast<float2*>(hi)[o / 2] = make_float2(h0, h1);
+    reinterpret_cast<float2*>(lo)[o / 2] = make_float2(v.x - h0, v.y - h1);
+  }
+}
+
+// Pack op(B) (K x N complex) into B' rows 2j = (Re, -Im), 2j+1 = (Im, Re), split hi/lo.
+__global__ void pack_b_kernel(const float2* __restrict__ B, long long b_rs, long long b_cs, int conj, int N, int K,
+                              int kpad, float* __restrict__ hi, float* __restrict__ lo) {
+  const long long total = (long long)N * (kpad / 2);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / (kpad / 2)), k = (int)(e % (kpad / 2));
+    float2 v = make_float2(0.f, 0.f);
+    if (k < K) { v = B[k * b_rs + j * b_cs]; if (conj) v.y = -v.y; }
+    float hr, hi_;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(hr) : "f"(v.x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(hi_) : "f"(v.y));
+    const float lr = v.x - hr, li = v.y - hi_;
+    const long long r0 = (long long)(2 * j) * kpad + 2 * k, r1 = r0 + kpad;
+    reinterpret_cast<float2*>(hi)[r0 / 2] = make_float2(hr, -hi_);
+    reinterpret_cast<float2*>(lo)[r0 / 2] = make_float2(lr, -li);
+    reinterpret_cast<float2*>(hi)[r1 / 2] = make_float2(hi_, hr);
+    reinterpret_cast<float2*>(lo)[r1 / 2] = make_float2(li, lr);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, float* base, int rows, int kpad) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 4};
+  cuuint32_t box[2] = {BKR, BM};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+inline int grid_for(long long work) {
+  long long g = (work + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(g, 8192));
+}
+
+}  // namespace
+
+struct TcGemm {
+  float *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  size_t cap = 0;   // floats per buffer
+};
+
+TcGemm* tc_create(size_t max_elems) {
+  TcGemm* g = new TcGemm();
+  // a packed operand holds 2 floats per complex entry, K padded to a multiple of 16 complex
+  g->cap = 4 * max_elems + 64 * 1024;
+  if (cudaMalloc(&g->ah, g->cap * 4) != cudaSuccess || cudaMalloc(&g->al, g->cap * 4) != cudaSuccess ||
+      cudaMalloc(&g->bh, g->cap * 4) != cudaSuccess || cudaMalloc(&g->bl, g->cap * 4) != cudaSuccess ||
+      !encode_fn()) {
+    tc_destroy(g);
+    return nullptr;
+  }
+  if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+    tc_destroy(g);
+    return nullptr;
+  }
+  return g;
+}
+
+void tc_destroy(TcGemm* g) {
+  if (!g) return;
+  if (g->ah) cudaFree(g->ah);
+  if (g->al) cudaFree(g->al);
+  if (g->bh) cudaFree(g->bh);
+  if (g->bl) cudaFree(g->bl);
+  delete g;
+}
+
+bool tc_fits(const TcGemm* g, int M, int N, int K) {
+  const size_t kpad = (size_t)((2 * K + BKR - 1) / BKR) * BKR;
+  return g && (size_t)M * kpad <= g->cap && (size_t)2 * N * kpad <= g->cap;
+}
+
+cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha, const float2* A, long long a_rs, long long a_cs,
+                    int conjA, const float2* B, long long b_rs, long long b_cs, int conjB, float2* C, long long c_rs,
+                    long long c_cs, cudaStream_t st, int* launched, int* status) {
+  *launched = 0;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (!tc_fits(g, M, N, K) || K <= 0) return cudaErrorInvalidValue;
+  const int kpad = ((2 * K + BKR - 1) / BKR) * BKR;
+  pack_a_kernel<<<grid_for((long long)M * kpad / 2), 256, 0, st>>>(A, a_rs, a_cs, conjA, M, K, kpad, g->ah, g->al);
+  pack_b_kernel<<<grid_for((long long)N * kpad / 2), 256, 0, st>>>(B, b_rs, b_cs, conjB, N, K, kpad, g->bh, g->bl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if (!make_map(&mAh, g->ah, M, kpad) || !make_map(&mAl, g->al, M, kpad) || !make_map(&mBh, g->bh, 2 * N, kpad) ||
+      !make_map(&mBl, g->bl, 2 * N, kpad))
+    return cudaErrorInvalidValue;
+  dim3 grid((2 * N + BN - 1) / BN, (M + BM - 1) / BM);
+  tc_gemm_kernel<<<grid, 128, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, kpad / BKR, alpha, C, c_rs, c_cs, status);
+  *launched = 3;
+  return cudaGetLastError();
 }
 
 }  // namespace eamps

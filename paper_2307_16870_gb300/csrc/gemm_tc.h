@@ -14,9 +14,14 @@ TcGemm* tc_create(size_t max_elems);
 void tc_destroy(TcGemm* g);
 
 // C = alpha * op(A) * op(B) with the strided conventions of cgemm_simt (complex64).
+// *launched receives the number of kernels launched; a device-side wait that
+// timed out sets ST_TIMEOUT in *status (device int).
 cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha,
                     const float2* A, long long a_rs, long long a_cs, int conjA,
                     const float2* B, long long b_rs, long long b_cs, int conjB,
-                    float2* C, long long c_rs, long long c_cs, cudaStream_t st, int* launched);
+                    float2* C, long long c_rs, long long c_cs, cudaStream_t st, int* launched, int* status);
+
+// Whether the workspace holds the packed operands of an M x K by K x N product.
+bool tc_fits(const TcGemm* g, int M, int N, int K);
 
 }  // namespace eamps

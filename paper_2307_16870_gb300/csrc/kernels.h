@@ -95,6 +95,10 @@ cudaError_t chain_contract(int N, const cplx<R>* const* sites, const int* bonds,
 template <class R>
 cudaError_t product_state(cplx<R>* const* sites, int N, int d, cudaStream_t st);
 
+// Convert complex128 to the working precision.
+template <class R>
+cudaError_t from_double(const double2* src, cplx<R>* dst, long long count, cudaStream_t st);
+
 // Convert a site to complex128.
 template <class R>
 cudaError_t to_double(const cplx<R>* src, double2* dst, long long count, cudaStream_t st);

@@ -369,6 +369,12 @@ __global__ void product_state_kernel(cplx<R>* const* sites, int N, int d) {
 }
 
 template <class R>
+__global__ void from_double_kernel(const double2* __restrict__ src, cplx<R>* __restrict__ dst, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = mk<R>((R)src[i].x, (R)src[i].y);
+}
+
+template <class R>
 __global__ void to_double_kernel(const cplx<R>* __restrict__ src, double2* __restrict__ dst, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
     dst[i] = make_double2((double)src[i].x, (double)src[i].y);
@@ -479,6 +485,12 @@ cudaError_t product_state(cplx<R>* const* sites, int N, int d, cudaStream_t st) 
 }
 
 template <class R>
+cudaError_t from_double(const double2* src, cplx<R>* dst, long long count, cudaStream_t st) {
+  from_double_kernel<R><<<grid_for(count, 256), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t to_double(const cplx<R>* src, double2* dst, long long count, cudaStream_t st) {
   to_double_kernel<R><<<grid_for(count, 256), 256, 0, st>>>(src, dst, count);
   return cudaGetLastError();
@@ -502,7 +514,8 @@ cudaError_t to_double(const cplx<R>* src, double2* dst, long long count, cudaStr
   template cudaError_t chain_contract<R>(int, const cplx<R>* const*, const int*, int, const double2*, int,      \
                                          const double2*, double2*, int, double2*, cudaStream_t);               \
   template cudaError_t to_double<R>(const cplx<R>*, double2*, long long, cudaStream_t);                        \
-  template cudaError_t product_state<R>(cplx<R>* const*, int, int, cudaStream_t);
+  template cudaError_t product_state<R>(cplx<R>* const*, int, int, cudaStream_t);                            \
+  template cudaError_t from_double<R>(const double2*, cplx<R>*, long long, cudaStream_t);
 
 EAMPS_INST(float)
 EAMPS_INST(double)
