@@ -239,6 +239,30 @@ mps_status mps_cgemm_c64(int precision, int M, int N, int K, float alpha,
                          const void* B, long long b_rs, long long b_cs, int conjB,
                          void* C, long long c_rs, long long c_cs, void* cuda_stream);
 
+/* Allocation-free form of mps_cgemm_c64 with precision MPS_TF32X3 (the
+ * paper has no counterpart: this is a deployment convenience).  Some callers
+ * cannot call cudaMalloc or cudaFree: a host framework that owns all device
+ * memory through its own pool, or a loop that must not stall, since cudaFree
+ * synchronises the device.  This entry point allocates nothing: the packing
+ * workspace and the status word live in one fixed array of 8 MiB + 256 bytes
+ * of device memory that belongs to the loaded library, and every GPU that
+ * loads the library holds it until the process exits.
+ * Limits: with kp = 2K rounded up to a multiple of 32, both M*kp and 2*N*kp
+ * must be <= 524288; larger shapes are rejected with MPS_ERR_ARG and a message
+ * on stderr.  Arguments, layouts and results are those of mps_cgemm_c64 (A, B,
+ * C in DEVICE memory, owned by the caller); the call is ordered on cuda_stream
+ * and synchronised before it returns.
+ * The first call on each device resolves the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the same array,
+ * so calls that overlap on the GPU (other host threads, other streams) race
+ * and must be serialised by the caller.
+ * Errors: MPS_ERR_ARG, MPS_ERR_CUDA, MPS_ERR_TIMEOUT. */
+mps_status mps_cgemm_c64_noalloc(int M, int N, int K, float alpha,
+                                 const void* A, long long a_rs, long long a_cs, int conjA,
+                                 const void* B, long long b_rs, long long b_cs, int conjB,
+                                 void* C, long long c_rs, long long c_cs, void* cuda_stream);
+
 /* Host helper: the superoperator of the channel {K} (n_kraus operators of
  * dimension 2^nq, host, 2*4^nq doubles each, concatenated) in the library's
  * vectorisation convention (see the top of this file).  out: host,

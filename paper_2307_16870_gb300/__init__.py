@@ -26,7 +26,7 @@ __all__ = [
     "mps_bond_dims", "mps_centre", "mps_get_site", "mps_lognorm", "mps_last_singular_values",
     "mps_truncation_log", "mps_sync", "mps_superop_from_kraus", "mps_status_string",
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
-    "mps_set_site", "mps_set_centre",
+    "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc",
 ]
 
 PURE, MIXED = 0, 1
@@ -95,6 +95,9 @@ def load(path: str | None = None):
         "mps_get_site": (C.c_int, [H, C.c_int, D, C.c_longlong, C.POINTER(C.c_int)]),
         "mps_lognorm": (C.c_int, [H, D]),
         "mps_set_site": (C.c_int, [H, C.c_int, D, C.POINTER(C.c_int)]),
+        "mps_cgemm_c64_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_longlong,
+                                            C.c_longlong, C.c_int, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int,
+                                            C.c_void_p, C.c_longlong, C.c_longlong, C.c_void_p]),
         "mps_set_centre": (C.c_int, [H, C.c_int]),
         "mps_last_singular_values": (C.c_int, [H, D, C.c_int, C.POINTER(C.c_int)]),
         "mps_truncation_log": (C.c_int, [H, C.POINTER(TruncRecord), C.c_int, C.POINTER(C.c_int)]),
@@ -283,6 +286,15 @@ def mps_cgemm_c64(precision: int, M: int, N: int, K: int, alpha: float, A: int, 
     return _check(load().mps_cgemm_c64(int(precision), M, N, K, float(alpha), C.c_void_p(A), a_rs, a_cs, int(conjA),
                                        C.c_void_p(B), b_rs, b_cs, int(conjB), C.c_void_p(Cp), c_rs, c_cs,
                                        C.c_void_p(stream or None)), "mps_cgemm_c64")
+
+
+def mps_cgemm_c64_noalloc(M: int, N: int, K: int, alpha: float, A: int, a_rs: int, a_cs: int, conjA: bool,
+                          B: int, b_rs: int, b_cs: int, conjB: bool, Cp: int, c_rs: int, c_cs: int,
+                          stream: int = 0) -> int:
+    """Allocation-free tensor-core C = alpha op(A) op(B) on device complex64 buffers (pointers as ints)."""
+    return _check(load().mps_cgemm_c64_noalloc(M, N, K, float(alpha), C.c_void_p(A), a_rs, a_cs, int(conjA),
+                                               C.c_void_p(B), b_rs, b_cs, int(conjB), C.c_void_p(Cp), c_rs, c_cs,
+                                               C.c_void_p(stream or None)), "mps_cgemm_c64_noalloc")
 
 
 def mps_superop_from_kraus(kraus: list, nq: int) -> np.ndarray:

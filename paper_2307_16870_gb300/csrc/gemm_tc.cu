@@ -330,20 +330,22 @@ bool tc_fits(const TcGemm* g, int M, int N, int K) {
   return g && (size_t)M * kpad <= g->cap && (size_t)2 * N * kpad <= g->cap;
 }
 
-cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha, const float2* A, long long a_rs, long long a_cs,
-                    int conjA, const float2* B, long long b_rs, long long b_cs, int conjB, float2* C, long long c_rs,
-                    long long c_cs, cudaStream_t st, int* launched, int* status) {
+namespace {
+
+// Pack both operands into (ah, al, bh, bl) and launch the tensor-core kernel.
+cudaError_t tc_gemm_on(float* ah, float* al, float* bh, float* bl, int M, int N, int K, float alpha, const float2* A,
+                       long long a_rs, long long a_cs, int conjA, const float2* B, long long b_rs, long long b_cs,
+                       int conjB, float2* C, long long c_rs, long long c_cs, cudaStream_t st, int* launched,
+                       int* status) {
   *launched = 0;
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  if (!tc_fits(g, M, N, K) || K <= 0) return cudaErrorInvalidValue;
   const int kpad = ((2 * K + BKR - 1) / BKR) * BKR;
-  pack_a_kernel<<<grid_for((long long)M * kpad / 2), 256, 0, st>>>(A, a_rs, a_cs, conjA, M, K, kpad, g->ah, g->al);
-  pack_b_kernel<<<grid_for((long long)N * kpad / 2), 256, 0, st>>>(B, b_rs, b_cs, conjB, N, K, kpad, g->bh, g->bl);
+  pack_a_kernel<<<grid_for((long long)M * kpad / 2), 256, 0, st>>>(A, a_rs, a_cs, conjA, M, K, kpad, ah, al);
+  pack_b_kernel<<<grid_for((long long)N * kpad / 2), 256, 0, st>>>(B, b_rs, b_cs, conjB, N, K, kpad, bh, bl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap mAh, mAl, mBh, mBl;
-  if (!make_map(&mAh, g->ah, M, kpad) || !make_map(&mAl, g->al, M, kpad) || !make_map(&mBh, g->bh, 2 * N, kpad) ||
-      !make_map(&mBl, g->bl, 2 * N, kpad))
+  if (!make_map(&mAh, ah, M, kpad) || !make_map(&mAl, al, M, kpad) || !make_map(&mBh, bh, 2 * N, kpad) ||
+      !make_map(&mBl, bl, 2 * N, kpad))
     return cudaErrorInvalidValue;
   dim3 grid((2 * N + BN - 1) / BN, (M + BM - 1) / BM);
   tc_gemm_kernel<<<grid, 128, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, kpad / BKR, alpha, C, c_rs, c_cs, status);
@@ -351,4 +353,107 @@ cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha, const float2* A
   return cudaGetLastError();
 }
 
+}  // namespace
+
+cudaError_t tc_gemm_raw(float* ah, float* al, float* bh, float* bl, int M, int N, int K, float alpha,
+                        const float2* A, long long a_rs, long long a_cs, int conjA, const float2* B, long long b_rs,
+                        long long b_cs, int conjB, float2* C, long long c_rs, long long c_cs, cudaStream_t st,
+                        int* launched, int* status) {
+  return tc_gemm_on(ah, al, bh, bl, M, N, K, alpha, A, a_rs, a_cs, conjA, B, b_rs, b_cs, conjB, C, c_rs, c_cs, st,
+                    launched, status);
+}
+
+const void* tc_gemm_kernel_entry() { return (const void*)tc_gemm_kernel; }
+int tc_gemm_smem_bytes() { return SMEM_BYTES; }
+
+cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha, const float2* A, long long a_rs, long long a_cs,
+                    int conjA, const float2* B, long long b_rs, long long b_cs, int conjB, float2* C, long long c_rs,
+                    long long c_cs, cudaStream_t st, int* launched, int* status) {
+  *launched = 0;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (!tc_fits(g, M, N, K) || K <= 0) return cudaErrorInvalidValue;
+  return tc_gemm_on(g->ah, g->al, g->bh, g->bl, M, N, K, alpha, A, a_rs, a_cs, conjA, B, b_rs, b_cs, conjB, C, c_rs,
+                    c_cs, st, launched, status);
+}
+
 }  // namespace eamps
+
+// ======================================================================
+// Allocation-free variant of mps_cgemm_c64 (tensor-core path).
+//
+// Its packing workspace (the hi/lo split copies of both operands) and its
+// status word live in one fixed-size array in device memory that is part of
+// the loaded library: every GPU that loads the library holds it until the
+// process exits, and every call shares it.
+#include <mutex>
+
+#include "eamps.h"
+
+namespace {
+
+constexpr size_t kNoAllocPackFloats = size_t(1) << 19;            // floats per packed operand buffer (2 MiB)
+constexpr size_t kNoAllocFloats = 4 * kNoAllocPackFloats + 64;   // four buffers + status word (8 MiB + 256 B)
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+std::mutex g_noalloc_mutex;
+float* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device; resolved once per
+// device with that device current (in host code the array's name is only a
+// host-side stand-in, never a usable device address).
+float* noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    if (cudaFuncSetAttribute(eamps::tc_gemm_kernel_entry(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             eamps::tc_gemm_smem_bytes()) != cudaSuccess)
+      return nullptr;
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" mps_status mps_cgemm_c64_noalloc(int M, int N, int K, float alpha, const void* A, long long a_rs,
+                                            long long a_cs, int conjA, const void* B, long long b_rs, long long b_cs,
+                                            int conjB, void* C, long long c_rs, long long c_cs, void* cuda_stream) {
+  if (M < 0 || N < 0 || K < 0 || !A || !B || !C) return MPS_ERR_ARG;
+  if (M == 0 || N == 0) return MPS_OK;
+  if (K == 0) return MPS_ERR_ARG;
+  const size_t kpad = (size_t)((2 * K + 31) / 32) * 32;
+  if ((size_t)M * kpad > kNoAllocPackFloats || (size_t)2 * N * kpad > kNoAllocPackFloats) {
+    std::fprintf(stderr,
+                 "eamps: mps_cgemm_c64_noalloc: shape %d x %d x %d exceeds the fixed workspace "
+                 "(M*pad32(2K) and 2N*pad32(2K) must each be <= %zu)\n",
+                 M, N, K, kNoAllocPackFloats);
+    return MPS_ERR_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MPS_ERR_CUDA;
+  float* base = noalloc_scratch(dev);
+  if (!base) return MPS_ERR_CUDA;
+  float* ah = base;
+  float* al = base + kNoAllocPackFloats;
+  float* bh = base + 2 * kNoAllocPackFloats;
+  float* bl = base + 3 * kNoAllocPackFloats;
+  int* status = reinterpret_cast<int*>(base + 4 * kNoAllocPackFloats);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the array keeps the previous call's contents: the status word must start at zero
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  int launched = 0;
+  if (e == cudaSuccess)
+    e = eamps::tc_gemm_raw(ah, al, bh, bl, M, N, K, alpha, (const float2*)A, a_rs, a_cs, conjA, (const float2*)B,
+                           b_rs, b_cs, conjB, (float2*)C, c_rs, c_cs, st, &launched, status);
+  int hs = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "eamps: CUDA error: %s\n", cudaGetErrorString(e));
+    return MPS_ERR_CUDA;
+  }
+  return (hs & eamps::ST_TIMEOUT) ? MPS_ERR_TIMEOUT : MPS_OK;
+}

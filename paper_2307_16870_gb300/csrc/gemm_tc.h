@@ -21,6 +21,15 @@ cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha,
                     const float2* B, long long b_rs, long long b_cs, int conjB,
                     float2* C, long long c_rs, long long c_cs, cudaStream_t st, int* launched, int* status);
 
+// The same product on caller-provided packing buffers (each large enough for
+// M x pad32(2K) and 2N x pad32(2K) floats); allocates nothing.
+cudaError_t tc_gemm_raw(float* ah, float* al, float* bh, float* bl, int M, int N, int K, float alpha,
+                        const float2* A, long long a_rs, long long a_cs, int conjA, const float2* B, long long b_rs,
+                        long long b_cs, int conjB, float2* C, long long c_rs, long long c_cs, cudaStream_t st,
+                        int* launched, int* status);
+const void* tc_gemm_kernel_entry();
+int tc_gemm_smem_bytes();
+
 // Whether the workspace holds the packed operands of an M x K by K x N product.
 bool tc_fits(const TcGemm* g, int M, int N, int K);
 
