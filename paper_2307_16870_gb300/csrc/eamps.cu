@@ -322,12 +322,15 @@ struct Engine final : mps_state {
       if ((s = copy(C, tmp, (size_t)m * n))) return s;
     } else {
       // X = C^dagger (column i = conj of row i of C), accumulate W (m x m):
-      // C^dagger W = Y  ->  C = W Y^dagger: Q = W, R = Y^dagger
+      // C^dagger W = Y  ->  C = W Y^dagger: Q = W with unit columns, R = Q^dagger C
       if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;
       if ((s = run_jacobi(n, m, true, X, n))) return s;
-      if ((s = gemm(m, n2, n, R(1), X, n, 1, 1, Nx, n2, 1, 0, T, n2, 1))) return s;        // Y^dagger A_{c+1}
+      if ((s = kl(column_norms<R>(Wacc, m, m, m, norms, stream)))) return s;
+      if ((s = extract(tmp, 1, m, m, m, Wacc, m, 1, nullptr, 0, norms, 0))) return s;      // Q row-major m x m
+      if ((s = gemm(m, n, m, R(1), tmp, 1, m, 1, C, n, 1, 0, tmp2, n, 1))) return s;       // R = Q^dagger C
+      if ((s = gemm(m, n2, n, R(1), tmp2, n, 1, 0, Nx, n2, 1, 0, T, n2, 1))) return s;     // R A_{c+1}
       if ((s = copy(Nx, T, (size_t)m * n2))) return s;
-      if ((s = extract(C, 1, m, m, m, Wacc, m, 1, nullptr, 0, nullptr, 0))) return s;       // Q = W, row-major m x m
+      if ((s = copy(C, tmp, (size_t)m * m))) return s;
       bonds[c + 1] = m;
     }
     centre = c + 1;
@@ -350,12 +353,16 @@ struct Engine final : mps_state {
       if ((s = copy(Pv, T, (size_t)m2 * m))) return s;
       if ((s = copy(C, tmp, (size_t)m * n))) return s;
     } else {
-      // X = C column-major, accumulate W (n x n): C W = Y -> C = Y W^dagger: Q' = W^dagger, L = Y
+      // X = C column-major, accumulate W (n x n): C W = Y -> C = Y W^dagger:
+      // Q' = W^dagger with unit rows, L = C Q'^dagger
       if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;
       if ((s = run_jacobi(m, n, true, X, m))) return s;
-      if ((s = gemm(m2, n, m, R(1), Pv, m, 1, 0, X, 1, m, 0, T, n, 1))) return s;          // A_{c-1} Y
+      if ((s = kl(column_norms<R>(Wacc, n, n, n, norms, stream)))) return s;
+      if ((s = extract(tmp, n, 1, n, n, Wacc, n, 1, nullptr, 1, norms, 0))) return s;      // Q' row-major n x n
+      if ((s = gemm(m, n, n, R(1), C, n, 1, 0, tmp, 1, n, 1, tmp2, n, 1))) return s;       // L = C Q'^dagger
+      if ((s = gemm(m2, n, m, R(1), Pv, m, 1, 0, tmp2, n, 1, 0, T, n, 1))) return s;       // A_{c-1} L
       if ((s = copy(Pv, T, (size_t)m2 * n))) return s;
-      if ((s = extract(C, n, 1, n, n, Wacc, n, 1, nullptr, 1, nullptr, 0))) return s;      // W^dagger row-major
+      if ((s = copy(C, tmp, (size_t)n * n))) return s;
       bonds[c] = n;
     }
     centre = c - 1;
@@ -432,37 +439,46 @@ struct Engine final : mps_state {
     if (right) mode = (n <= m) ? R_COLS : R_ROWS_ACC;
     else mode = (m <= n) ? L_ROWS : L_COLS_ACC;
     const bool cols = (mode == R_COLS || mode == L_COLS_ACC);     // X = theta (else theta^dagger)
-    const bool need_theta = (mode == R_COLS || mode == L_ROWS);
     const int l = cols ? m : n, c = cols ? n : m;
-    if ((s = kl(gate_theta<R>(T, cl, d, cr, G, X, cols ? 0 : 1, need_theta ? theta : nullptr, stream)))) return s;
-    // (a2) SVD
+    if ((s = kl(gate_theta<R>(T, cl, d, cr, G, X, cols ? 0 : 1, theta, stream)))) return s;
+    // (a2) SVD: one-sided Jacobi gives the singular directions
     const bool acc = (mode == R_ROWS_ACC || mode == L_COLS_ACC);
     if ((s = run_jacobi(l, c, acc, X, l))) return s;
+    // Directions D with unit columns (FP64 norms): left vectors U (m x c) for a rightward
+    // update, right vectors V (n x c) for a leftward one; from the rotated columns, or from
+    // the accumulated rotations when the Jacobi ran on the other side.
+    const bool u_type = right;
+    {
+      const Z* src = acc ? Wacc : X;
+      const int len = acc ? c : l;
+      if ((s = kl(column_norms<R>(src, len, len, c, norms, stream)))) return s;
+      if (u_type)   // U row-major (m x c)
+        s = extract(tmp, 1, c, c, m, src, len, 1, nullptr, 0, norms, 0);
+      else          // V column-major (n x c)
+        s = extract(tmp, n, 1, c, n, src, len, 1, nullptr, 0, norms, 0);
+      if (s) return s;
+    }
+    // Refinement: singular values from the original theta, P = U^dagger theta (c x n, row-major;
+    // row j = s_j v_j^dagger) or P = theta V (m x c, column-major; column j = s_j u_j), FP64 norms.
+    // The rotations' rounding drift in FP32 column norms does not reach these values.
+    if (u_type) { if ((s = gemm(c, n, m, R(1), tmp, 1, c, 1, theta, n, 1, 0, tmp2, n, 1))) return s; }
+    else { if ((s = gemm(m, c, n, R(1), theta, n, 1, 0, tmp, 1, n, 0, tmp2, 1, m))) return s; }
+    const long long pld = u_type ? n : m;
+    const int plen = u_type ? n : m;
     // (a3) selection and FP64 bookkeeping
-    if ((s = kl(select_bond<R>(X, l, l, c, ctrl, target, s_sorted, perm, stream)))) return s;
+    if ((s = kl(select_bond<R>(tmp2, pld, plen, c, ctrl, target, s_sorted, perm, stream)))) return s;
     if ((s = read_ctrl())) return s;
     const int k = hctrl->k;
-    const R inv_sqrt_wk = (R)(1.0 / std::sqrt(hctrl->Wk));
     Z* Aq = site[q];
     Z* Ap = site[q + 1];
-    // (a4) write-back: A_q (cl, d, k) row-major, A_{q+1} (k, d, cr) row-major
-    switch (mode) {
-      case R_COLS:   // U = Y/s; S V^dagger = U^dagger theta
-        if ((s = extract(Aq, 1, k, k, m, X, l, 1, perm, 0, s_sorted, 0))) return s;
-        if ((s = gemm(k, n, m, inv_sqrt_wk, Aq, 1, k, 1, theta, n, 1, 0, Ap, n, 1))) return s;
-        break;
-      case L_ROWS:   // V = Y/s (Y columns are conj rows of theta); U S = theta V
-        if ((s = extract(Ap, n, 1, k, n, X, l, 1, perm, 1, s_sorted, 0))) return s;
-        if ((s = gemm(m, k, n, inv_sqrt_wk, theta, n, 1, 0, Ap, 1, n, 1, Aq, k, 1))) return s;
-        break;
-      case R_ROWS_ACC:   // theta = W Y^dagger: U = W, S V^dagger = Y^dagger
-        if ((s = extract(Aq, 1, k, k, m, Wacc, c, 1, perm, 0, nullptr, 0))) return s;
-        if ((s = extract(Ap, n, 1, k, n, X, l, 1, perm, 1, nullptr, 1))) return s;
-        break;
-      case L_COLS_ACC:   // theta = Y W^dagger: U S = Y, V = W
-        if ((s = extract(Aq, 1, k, k, m, X, l, 1, perm, 0, nullptr, 1))) return s;
-        if ((s = extract(Ap, n, 1, k, n, Wacc, c, 1, perm, 1, nullptr, 0))) return s;
-        break;
+    // (a4) write-back: A_q (cl, d, k) row-major, A_{q+1} (k, d, cr) row-major; the kept
+    // singular values are renormalised by 1/sqrt(W_k)
+    if (u_type) {   // A_q = U[:, perm], A_{q+1} = P[perm, :] / sqrt(W_k)
+      if ((s = extract(Aq, 1, k, k, m, tmp, 1, c, perm, 0, nullptr, 0))) return s;
+      if ((s = extract(Ap, n, 1, k, n, tmp2, n, 1, perm, 0, nullptr, 1))) return s;
+    } else {        // A_q = P[:, perm] / sqrt(W_k), A_{q+1} = V[:, perm]^dagger
+      if ((s = extract(Aq, 1, k, k, m, tmp2, m, 1, perm, 0, nullptr, 1))) return s;
+      if ((s = extract(Ap, n, 1, k, n, tmp, n, 1, perm, 1, nullptr, 0))) return s;
     }
     bonds[q + 1] = k;
     centre = right ? q + 1 : q;

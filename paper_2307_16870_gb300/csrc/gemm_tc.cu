@@ -10,14 +10,17 @@
 // and D = Ahi Bhi + Ahi Blo + Alo Bhi accumulates in FP32 in tensor memory:
 // FP32-level accuracy from kind::tf32 MMAs.
 //
-// Kernel: one CTA per 128 x 128 tile of D, four warps.  Warp 0 (one lane)
+// Kernel: one CTA per 128 x 128 tile of D, six warps.  Warp 0 (one lane)
 // drives TMA loads of 32-wide K blocks (128-byte swizzled, K-major) into a
 // three-stage shared-memory ring; warp 1 (one lane) issues 12 tcgen05.mma per
-// block (3 products x 4 K-steps of 8) into a 128-column TMEM accumulator and
-// releases each stage with tcgen05.commit; all four warps then read the
-// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31) and store
-// complex results with the caller's strides and scale.  Every mbarrier wait
-// is bounded; a timeout sets the status bit and the CTA drains and returns.
+// block (3 products x 4 K-steps of 8) into one of two 128-column TMEM
+// accumulators and releases the stage and the accumulator with
+// tcgen05.commit; warps 2-5 (warp w owns TMEM lanes 32*(w%4)..+31) read each
+// block's partial product with tcgen05.ld and add it into FP32 registers.
+// The tensor core's own accumulation truncates (a bias of about -1e-8 K
+// relative, measured); summing one K block at a time on the CUDA cores keeps
+// the product at FP32 accuracy.  Every mbarrier wait is bounded; a timeout
+// sets the status bit and the CTA drains its copies and MMAs and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -121,16 +124,38 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh,
-                                                         const __grid_constant__ CUtensorMap mAl,
-                                                         const __grid_constant__ CUtensorMap mBh,
-                                                         const __grid_constant__ CUtensorMap mBl,
-                                                         int M, int N, int nkb, float alpha,
-                                                         float2* __restrict__ C, long long c_rs, long long c_cs,
-                                                         int* status) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another role of the CTA aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, int* status,
+                                                   volatile int* abort_flag) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if ((i & 255) == 255 && *abort_flag) return false;
+    if (i > 64) __nanosleep(20);
+  }
+  atomicOr(status, ST_TIMEOUT);
+  *abort_flag = 1;
+  return false;
+}
+
+constexpr int NTHREADS = 192;          // warp 0: TMA, warp 1: MMA, warps 2-5: accumulation + epilogue
+constexpr uint32_t TMEM_COLS = 256;    // two 128-column FP32 accumulators (ping-pong)
+
+__global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh,
+                                                              const __grid_constant__ CUtensorMap mAl,
+                                                              const __grid_constant__ CUtensorMap mBh,
+                                                              const __grid_constant__ CUtensorMap mBl,
+                                                              int M, int N, int nkb, float alpha,
+                                                              float2* __restrict__ C, long long c_rs, long long c_cs,
+                                                              int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_full[2];
+  __shared__ __align__(8) uint64_t acc_empty[2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
@@ -138,16 +163,18 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM;
   const int n0 = blockIdx.x * BN;   // real columns of D
+  volatile int* abortp = &abort_s;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); }
     mbar_init(&done_bar, 1);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base_s)),
-                 "r"(128u));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -156,72 +183,95 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   const uint32_t tmem = tmem_base_s;
   constexpr uint32_t IDESC = idesc_tf32(BM, BN);
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1, status)) { abort_s = 1; break; }
-      unsigned char* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-      tma_load_2d(st + 0 * TILE_BYTES, &mAh, &full_bar[s], kb * BKR, m0);
-      tma_load_2d(st + 1 * TILE_BYTES, &mAl, &full_bar[s], kb * BKR, m0);
-      tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full_bar[s], kb * BKR, n0);
-      tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full_bar[s], kb * BKR, n0);
-      issued = kb + 1;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait_or_abort(&empty_bar[s], ((kb / STAGES) - 1) & 1, status, abortp)) break;
+        unsigned char* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+        tma_load_2d(st + 0 * TILE_BYTES, &mAh, &full_bar[s], kb * BKR, m0);
+        tma_load_2d(st + 1 * TILE_BYTES, &mAl, &full_bar[s], kb * BKR, m0);
+        tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full_bar[s], kb * BKR, n0);
+        tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full_bar[s], kb * BKR, n0);
+        issued = kb + 1;
+      }
+      // every issued copy must land before the CTA may exit
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, status);
     }
-    // drain: every issued stage must have landed before the CTA may exit
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-      mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, status);
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer: one K block per accumulator, buffers alternate
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES, b = kb & 1;
+        if (!mbar_wait_or_abort(&full_bar[s], (kb / STAGES) & 1, status, abortp)) break;
+        if (kb >= 2 && !mbar_wait_or_abort(&acc_empty[b], ((kb >> 1) - 1) & 1, status, abortp)) break;
+        tc_fence_after();
+        const uint32_t base = su32(smem + s * STAGE_BYTES);
+        const uint64_t dAh = sdesc(base), dAl = sdesc(base + TILE_BYTES);
+        const uint64_t dBh = sdesc(base + 2 * TILE_BYTES), dBl = sdesc(base + 3 * TILE_BYTES);
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+#pragma unroll
+        for (int kk = 0; kk < BKR / 8; ++kk) {
+          const uint64_t adv = (uint64_t)((kk * 32) >> 4);   // 8 TF32 = 32 bytes along K
+          mma_tf32(d, dAl + adv, dBh + adv, IDESC, kk > 0 ? 1u : 0u);
+          mma_tf32(d, dAh + adv, dBl + adv, IDESC, 1u);
+          mma_tf32(d, dAh + adv, dBh + adv, IDESC, 1u);
+        }
+        mma_commit(&empty_bar[s]);
+        mma_commit(&acc_full[b]);
+      }
+      mma_commit(&done_bar);   // arrives once every MMA issued above has completed
+    }
+  } else {
+    // ---------------- accumulation (promotion) and epilogue: warp w reads TMEM lanes 32*(w%4)..
+    // Each K block's partial product is added into FP32 registers with round-to-nearest adds,
+    // so the tensor core accumulates over one block only.
+    const int qd = warp & 3;
+    float acc[BN];
+#pragma unroll
+    for (int i = 0; i < BN; ++i) acc[i] = 0.f;
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, status)) { ok = false; break; }
+      const int b = kb & 1;
+      if (!mbar_wait_or_abort(&acc_full[b], (kb >> 1) & 1, status, abortp)) { ok = false; break; }
       tc_fence_after();
-      const uint32_t base = su32(smem + s * STAGE_BYTES);
-      const uint64_t dAh = sdesc(base), dAl = sdesc(base + TILE_BYTES);
-      const uint64_t dBh = sdesc(base + 2 * TILE_BYTES), dBl = sdesc(base + 3 * TILE_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BKR / 8; ++kk) {
-        const uint64_t adv = (uint64_t)((kk * 32) >> 4);   // 8 TF32 = 32 bytes along K
-        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, dAl + adv, dBh + adv, IDESC, acc);
-        mma_tf32(tmem, dAh + adv, dBl + adv, IDESC, 1u);
-        mma_tf32(tmem, dAh + adv, dBh + adv, IDESC, 1u);
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN + ch * 32), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[ch * 32 + i] += __uint_as_float(v[i]);
       }
-      mma_commit(&empty_bar[s]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
-    if (!ok) abort_s = 1;
-    mma_commit(&done_bar);   // arrives once every MMA issued above has completed
-  }
-  __syncthreads();
-  // ---------------- epilogue (all four warps)
-  const bool done = mbar_wait(&done_bar, 0, status);
-  tc_fence_after();
-  if (done && !abort_s) {
-    const int row = m0 + warp * 32 + lane;
-    for (int ch = 0; ch < BN / 32; ++ch) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+    if (ok && !*abortp) {
+      const int row = m0 + qd * 32 + lane;
       if (row < M) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int j = (n0 + ch * 32) / 2 + c;
+        for (int c = 0; c < BN / 2; ++c) {
+          const int j = n0 / 2 + c;
           if (j < N) {
             float2 z;
-            z.x = alpha * __uint_as_float(v[2 * c]);
-            z.y = alpha * __uint_as_float(v[2 * c + 1]);
+            z.x = alpha * acc[2 * c];
+            z.y = alpha * acc[2 * c + 1];
             C[(long long)row * c_rs + (long long)j * c_cs] = z;
           }
         }
       }
     }
   }
-  tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+  // no MMA may still write TMEM when it is released
+  mbar_wait(&done_bar, 0, status);
+  tc_fence_after();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 // Pack op(A) (M x K complex) into interleaved real rows, split hi/lo: ld = kpad reals.
@@ -348,7 +398,8 @@ cudaError_t tc_gemm_on(float* ah, float* al, float* bh, float* bl, int M, int N,
       !make_map(&mBl, bl, 2 * N, kpad))
     return cudaErrorInvalidValue;
   dim3 grid((2 * N + BN - 1) / BN, (M + BM - 1) / BM);
-  tc_gemm_kernel<<<grid, 128, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, kpad / BKR, alpha, C, c_rs, c_cs, status);
+  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, kpad / BKR, alpha, C, c_rs, c_cs,
+                                                     status);
   *launched = 3;
   return cudaGetLastError();
 }
