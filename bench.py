@@ -292,7 +292,8 @@ def run_ours(a) -> int:
             "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, not measured)",
             "share_of_step": (st["jacobi_ms"] / sum(step_ms)) if step_ms else None,
             "launches": st["jacobi_launches"], "avg_launch_ms": st["jacobi_ms"] / max(st["jacobi_launches"], 1),
-            "sweeps_per_launch": st["jacobi_sweeps"] / max(st["jacobi_launches"], 1)}
+            "sweeps_per_launch": st["jacobi_sweeps"] / max(st["jacobi_launches"], 1),
+            "centre_move_share": (st["move_jacobi_ms"] / st["jacobi_ms"]) if st["jacobi_ms"] else None}
     gemm = {"launches": st["gemm_launches"], "ms": st["gemm_ms"],
             "tflops": (st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12) if st["gemm_ms"] > 0 else None}
     cpu = None

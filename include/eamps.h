@@ -216,6 +216,8 @@ typedef struct {
   double gemm_ms;
   double gemm_flops;           /* 8 M N K per complex GEMM */
   long long gates;             /* two-qubit updates applied */
+  long long move_jacobi_launches;  /* Jacobi launches of centre moves (included in jacobi_*) */
+  double move_jacobi_ms;           /* their summed event durations (profiling on) */
 } mps_stats_t;
 
 /* Switch event timing of the Jacobi and contraction launches on (1) or off (0). */

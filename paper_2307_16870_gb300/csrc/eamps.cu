@@ -108,11 +108,16 @@ struct Engine final : mps_state {
   DevCtrl* hctrl = nullptr;
   double2 *wdev = nullptr, *w2dev = nullptr, *work = nullptr, *outdev = nullptr, *hout = nullptr;
   double2* stage = nullptr;   // complex128 staging of one site (mps_get_site)
+  Z* xch = nullptr;           // Jacobi exchange slots
+  size_t xch_cap = 0;
+  unsigned* jflags = nullptr; // Jacobi position flags
+  static constexpr int kFlagsCap = 4096;
   size_t site_cap = 0;
   TcGemm* tc = nullptr;
   // statistics
-  long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0;
-  double gemm_flops = 0.0, jac_ms = 0.0, gemm_ms = 0.0;
+  long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0, n_jac_move = 0;
+  double gemm_flops = 0.0, jac_ms = 0.0, gemm_ms = 0.0, jac_move_ms = 0.0;
+  bool in_move = false;
   bool prof = false;
   struct Timed { cudaEvent_t a, b; int kind; };
   std::vector<Timed> pending;
@@ -121,7 +126,7 @@ struct Engine final : mps_state {
   ~Engine() override {
     if (stream) cudaStreamSynchronize(stream);
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
-                    ctrl, wdev, w2dev, work, outdev, stage};
+                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags};
     for (void* b : bufs) if (b) cudaFree(b);
     if (hctrl) cudaFreeHost(hctrl);
     if (hout) cudaFreeHost(hout);
@@ -153,7 +158,13 @@ struct Engine final : mps_state {
   void harvest() {
     for (auto& t : pending) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) (t.kind == 0 ? jac_ms : gemm_ms) += ms;
+      if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+        if (t.kind == 1) gemm_ms += ms;
+        else {
+          jac_ms += ms;
+          if (t.kind == 2) jac_move_ms += ms;
+        }
+      }
       ev_pool.push_back(t.a);
       ev_pool.push_back(t.b);
     }
@@ -212,6 +223,10 @@ struct Engine final : mps_state {
         !dalloc(&wdev, (size_t)N * d) || !dalloc(&w2dev, 16) || !dalloc(&work, (size_t)(2 + d) * (chi_cap + 8)) ||
         !dalloc(&outdev, 4) || !dalloc(&stage, site_max))
       return MPS_ERR_OOM;
+    // exchange slots: 2 parities x (columns + padding of one block per CTA) x column length,
+    // column length at most the longer side plus accumulated rotations
+    xch_cap = (size_t)2 * ((size_t)c_max + 2 * 64) * (size_t)(2 * c_max);
+    if (!dalloc(&xch, xch_cap) || !dalloc(&jflags, kFlagsCap)) return MPS_ERR_OOM;
     site_cap = site_max;
     if (cudaMallocHost((void**)&hctrl, sizeof(DevCtrl)) != cudaSuccess) return MPS_ERR_OOM;
     if (cudaMallocHost((void**)&hout, sizeof(double2) * 4) != cudaSuccess) return MPS_ERR_OOM;
@@ -279,16 +294,18 @@ struct Engine final : mps_state {
       if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
     if (c <= 1) return MPS_OK;
     JacobiPlan plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count);
-    const int fit = jacobi_max_ctas<R>(plan.smem);
+    const int fit = jacobi_max_ctas<R>(plan);
     if (fit <= 0) return MPS_ERR_CUDA;
     if (plan.nb / 2 > fit) {
       plan = jacobi_plan<R>(l, c, acc, sm_count, fit);
       if (plan.nb / 2 > fit) return MPS_ERR_ARG;
     }
     ++n_jac;
+    if (in_move) ++n_jac_move;
     const int id = tbegin();
-    mps_status s = kl(jacobi_launch<R>(plan, Xp, ldx, l, c, acc ? Wacc : nullptr, c, opt.max_sweeps, ctrl, stream));
-    tend(id, 0);
+    mps_status s = kl(jacobi_launch<R>(plan, Xp, ldx, l, c, acc ? Wacc : nullptr, c, opt.max_sweeps, ctrl, xch,
+                                       xch_cap, jflags, kFlagsCap, stream));
+    tend(id, in_move ? 2 : 0);
     return s;
   }
 
@@ -370,11 +387,12 @@ struct Engine final : mps_state {
   }
 
   mps_status move_to(int to) {
-    while (centre < to)
-      if (mps_status s = move_right(centre)) return s;
-    while (centre > to)
-      if (mps_status s = move_left(centre)) return s;
-    return MPS_OK;
+    in_move = true;
+    mps_status s = MPS_OK;
+    while (!s && centre < to) s = move_right(centre);
+    while (!s && centre > to) s = move_left(centre);
+    in_move = false;
+    return s;
   }
 
   // ------------------------------------------------------------- operators
@@ -549,6 +567,8 @@ struct Engine final : mps_state {
     out->gemm_ms = gemm_ms;
     out->gemm_flops = gemm_flops;
     out->gates = n_gates;
+    out->move_jacobi_launches = n_jac_move;
+    out->move_jacobi_ms = jac_move_ms;
     return s;
   }
 
@@ -556,8 +576,8 @@ struct Engine final : mps_state {
     mps_status s;
     if ((s = cu(cudaStreamSynchronize(stream)))) return s;
     harvest();
-    n_launch = n_jac = n_gemm = n_gates = 0;
-    gemm_flops = jac_ms = gemm_ms = 0.0;
+    n_launch = n_jac = n_gemm = n_gates = n_jac_move = 0;
+    gemm_flops = jac_ms = gemm_ms = jac_move_ms = 0.0;
     const size_t off = offsetof(DevCtrl, jac_sweeps);
     if ((s = cu(cudaMemsetAsync((char*)ctrl + off, 0, sizeof(DevCtrl) - off, stream)))) return s;
     return cu(cudaStreamSynchronize(stream));

@@ -18,8 +18,10 @@
 //  * A pair is rotated only when |a^dagger b| > tol |a||b|, tol = 4 sqrt(l)
 //    eps: below that the inner product is rounding noise.
 #include <algorithm>
-#include <cmath>
 #include <cfloat>
+#include <cmath>
+#include <cstdlib>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -73,7 +75,43 @@ struct JArgs {
   cplx<R>* W; long long ldw;
   int w; int nb; int max_sweeps; R tol;
   DevCtrl* ctrl;
+  cplx<R>* xch;        // exchange slots: [2 parities][nb positions][w columns][L]
+  unsigned* flags;     // per position: 1 + the last round whose block was published
 };
+
+__device__ __forceinline__ void st_release(unsigned* a, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_release(unsigned* a, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
+  return old;
+}
+
+// Thread 0 waits (bounded) until *a >= target; the whole CTA then proceeds.
+__device__ __forceinline__ bool cta_wait_geq(const unsigned* a, unsigned target, DevCtrl* ctrl) {
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    long long spins = 0;
+    while (ld_acquire(a) < target) {
+      if (++spins > 64) __nanosleep(20);
+      if (spins > kSpinLimit || (*(volatile int*)&ctrl->status & ST_TIMEOUT)) {
+        atomicOr(&ctrl->status, ST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
 
 template <class R>
 __device__ void load_pair(const JArgs<R>& p, cplx<R>* slots, int* gcol, int L, int bA, int bB) {
@@ -83,13 +121,21 @@ __device__ void load_pair(const JArgs<R>& p, cplx<R>* slots, int* gcol, int L, i
     gcol[s] = g < p.c ? g : -1;
   }
   __syncthreads();
-  const long long total = (long long)2 * w * L;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    int s = (int)(e / L), i = (int)(e % L);
-    int g = gcol[s];
-    cplx<R> v = mk<R>(0, 0);
-    if (g >= 0) v = (i < p.l) ? p.X[g * p.ldx + i] : p.W[g * p.ldw + (i - p.l)];
-    slots[(long long)s * L + i] = v;
+  // one warp per column, lanes along the rows (coalesced, no index division)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int s = warp; s < 2 * w; s += nwarps) {
+    const int g = gcol[s];
+    cplx<R>* dst = slots + (long long)s * L;
+    if (g < 0) {
+      for (int i = lane; i < L; i += 32) dst[i] = mk<R>(0, 0);
+      continue;
+    }
+    const cplx<R>* xs = p.X + (long long)g * p.ldx;
+    for (int i = lane; i < p.l; i += 32) dst[i] = __ldcg(xs + i);
+    if (p.W) {
+      const cplx<R>* ws = p.W + (long long)g * p.ldw;
+      for (int i = lane; i < p.c; i += 32) dst[p.l + i] = __ldcg(ws + i);
+    }
   }
   __syncthreads();
 }
@@ -97,13 +143,17 @@ __device__ void load_pair(const JArgs<R>& p, cplx<R>* slots, int* gcol, int L, i
 template <class R>
 __device__ void store_pair(const JArgs<R>& p, const cplx<R>* slots, const int* gcol, int L) {
   const int w = p.w;
-  const long long total = (long long)2 * w * L;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    int s = (int)(e / L), i = (int)(e % L);
-    int g = gcol[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int s = warp; s < 2 * w; s += nwarps) {
+    const int g = gcol[s];
     if (g < 0) continue;
-    cplx<R> v = slots[(long long)s * L + i];
-    if (i < p.l) p.X[g * p.ldx + i] = v; else p.W[g * p.ldw + (i - p.l)] = v;
+    const cplx<R>* src = slots + (long long)s * L;
+    cplx<R>* xd = p.X + (long long)g * p.ldx;
+    for (int i = lane; i < p.l; i += 32) __stcg(xd + i, src[i]);
+    if (p.W) {
+      cplx<R>* wd = p.W + (long long)g * p.ldw;
+      for (int i = lane; i < p.c; i += 32) __stcg(wd + i, src[p.l + i]);
+    }
   }
   __syncthreads();
 }
@@ -187,75 +237,432 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JArgs<R> p) {
   }
 }
 
+
+// Register-resident kernel with point-to-point exchange.  CTA i always holds
+// the positions i (block A) and nb-1-i (block B) of the circle-method
+// tournament; after every round the blocks shift by one position, so each
+// CTA takes its next blocks from its two neighbours.  A CTA publishes its two
+// blocks into double-buffered exchange slots and releases a per-position
+// flag; its neighbours acquire the flag before reading.  Double buffering is
+// enough because every writer also reads from the CTA that reads its slot,
+// so it cannot finish two rounds before that reader has taken the block.  The
+// only grid-wide synchronisation is one counter barrier per sweep for the
+// convergence vote.
+template <class R, int NW, int RPL, int AP>
+__global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = p.w, nb = p.nb, P = nb / 2;
+  const int L = p.l + (p.W ? p.c : 0);
+  const int l = p.l;
+  cplx<R>* slots = reinterpret_cast<cplx<R>*>(smem_raw);
+  int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * L);
+  __shared__ unsigned rot_s;
+  __shared__ unsigned total_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cta = blockIdx.x;
+  const int pos[2] = {cta, nb - 1 - cta};
+  const int wpad = w + (w & 1);
+  unsigned long long rot_total = 0;
+  bool converged = false;
+  int sweep = 0;
+  unsigned rnd = 0;   // rounds completed over all sweeps
+
+  // round 0 of the first sweep: position q holds player q
+  for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
+    const int g = pos[s / w] * w + (s % w);
+    gcol[s] = g < p.c ? g : -1;
+  }
+  __syncthreads();
+  for (int s = warp; s < 2 * w; s += NW) {
+    const int g = gcol[s];
+    cplx<R>* dst = slots + (long long)s * L;
+    if (g < 0) { for (int i = lane; i < L; i += 32) dst[i] = mk<R>(0, 0); continue; }
+    const cplx<R>* xs = p.X + (long long)g * p.ldx;
+    for (int i = lane; i < l; i += 32) dst[i] = __ldcg(xs + i);
+    if (p.W) {
+      const cplx<R>* ws = p.W + (long long)g * p.ldw;
+      for (int i = lane; i < p.c; i += 32) dst[l + i] = __ldcg(ws + i);
+    }
+  }
+  __syncthreads();
+
+  for (sweep = 0; sweep < p.max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rot_s = 0;
+    __syncthreads();
+    for (int r = 0; r < nb - 1; ++r, ++rnd) {
+      if (rnd > 0 && P > 1) {
+        // take the blocks that moved into my positions
+        for (int h = 0; h < 2; ++h) {
+          if (pos[h] == 0) continue;                      // block 0 never moves
+          const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
+          if (!cta_wait_geq(p.flags + src, rnd, p.ctrl)) return;
+          const cplx<R>* from = p.xch + ((long long)((rnd - 1) & 1) * nb + src) * w * L;
+          for (int s = warp; s < w; s += NW) {
+            cplx<R>* dst = slots + (long long)(h * w + s) * L;
+            const cplx<R>* sp = from + (long long)s * L;
+            for (int i = lane; i < L; i += 32) dst[i] = __ldcg(sp + i);
+          }
+        }
+        for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
+          const int g = rr_player(nb, r, pos[s / w]) * w + (s % w);
+          gcol[s] = g < p.c ? g : -1;
+        }
+        __syncthreads();
+      }
+      unsigned my_rot = 0;
+      if (r == 0) {
+        const int half = wpad / 2;
+        for (int t = 0; t < wpad - 1; ++t) {
+          for (int pi = warp; pi < 2 * half; pi += NW) {
+            const int blk = pi / half, i = pi % half;
+            int s1 = rr_player(wpad, t, i), s2 = rr_player(wpad, t, wpad - 1 - i);
+            if (s1 >= w || s2 >= w) continue;
+            s1 += blk * w; s2 += blk * w;
+            if (gcol[s1] < 0 || gcol[s2] < 0) continue;
+            my_rot += rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, l, L, p.tol, lane);
+          }
+          __syncthreads();
+        }
+      }
+      // cross phase: warp owns A columns warp*AP + a in registers
+      cplx<R> A[AP][RPL], B[AP][RPL];
+#pragma unroll
+      for (int a = 0; a < AP; ++a) {
+        const cplx<R>* src = slots + (long long)(warp * AP + a) * L;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const int row = lane + 32 * k;
+          A[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
+        }
+      }
+      for (int t = 0; t < w; ++t) {
+        int sb[AP];
+        bool val[AP];
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          const int ia = warp * AP + a;
+          sb[a] = w + (ia + t) % w;
+          val[a] = gcol[ia] >= 0 && gcol[sb[a]] >= 0;
+          const cplx<R>* src = slots + (long long)sb[a] * L;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const int row = lane + 32 * k;
+            B[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
+          }
+        }
+        R da[AP], db[AP], gr[AP], gi[AP];
+        // packed two-wide FP32 (FFMA2): accumulate (x.re*y.re, x.im*y.im) style pairs
+        float2 d2a[AP], d2b[AP], g2a[AP], g2b[AP];
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          d2a[a] = make_float2(0.f, 0.f); d2b[a] = d2a[a]; g2a[a] = d2a[a]; g2b[a] = d2a[a];
+        }
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          if (lane + 32 * k < l) {
+#pragma unroll
+            for (int a = 0; a < AP; ++a) {
+              const float2 u = A[a][k], v = B[a][k];
+              d2a[a] = __ffma2_rn(u, u, d2a[a]);                         // (u.re^2, u.im^2)
+              d2b[a] = __ffma2_rn(v, v, d2b[a]);
+              g2a[a] = __ffma2_rn(u, v, g2a[a]);                         // (u.re v.re, u.im v.im)
+              g2b[a] = __ffma2_rn(u, make_float2(v.y, v.x), g2b[a]);      // (u.re v.im, u.im v.re)
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          da[a] = d2a[a].x + d2a[a].y;
+          db[a] = d2b[a].x + d2b[a].y;
+          gr[a] = g2a[a].x + g2a[a].y;          // Re(u^dagger v)
+          gi[a] = g2b[a].x - g2b[a].y;          // Im(u^dagger v)
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int a = 0; a < AP; ++a) {
+            da[a] += __shfl_xor_sync(0xffffffffu, da[a], o);
+            db[a] += __shfl_xor_sync(0xffffffffu, db[a], o);
+            gr[a] += __shfl_xor_sync(0xffffffffu, gr[a], o);
+            gi[a] += __shfl_xor_sync(0xffffffffu, gi[a], o);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          const R g = sqrt(gr[a] * gr[a] + gi[a] * gi[a]);
+          const bool rot = val[a] && (da[a] > 0) && (db[a] > 0) && (g > p.tol * sqrt(da[a]) * sqrt(db[a]));
+          if (rot) {
+            const R zeta = (db[a] - da[a]) / (2 * g);
+            const R tt = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+            const R cs = R(1) / sqrt(R(1) + tt * tt);
+            const R sn = cs * tt;
+            const R er = gr[a] / g, ei = gi[a] / g;
+            cplx<R>* dst = slots + (long long)sb[a] * L;
+            // x' = cs x - sn e^{-i phi} y = cs x - al y - be (y.im, -y.re)
+            // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al = sn er, be = sn ei
+            const float al = sn * er, be = sn * ei;
+            const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
+            const float2 mbe = make_float2(-be, be), pbe = make_float2(-be, be);
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const float2 u = A[a][k], v = B[a][k];
+              float2 nu = __fmul2_rn(u, csv);
+              nu = __ffma2_rn(v, mal, nu);
+              nu = __ffma2_rn(make_float2(v.y, v.x), mbe, nu);
+              float2 nv = __fmul2_rn(v, csv);
+              nv = __ffma2_rn(u, pal, nv);
+              nv = __ffma2_rn(make_float2(u.y, u.x), pbe, nv);
+              A[a][k] = nu;
+              const int row = lane + 32 * k;
+              if (row < L) dst[row] = nv;
+            }
+            ++my_rot;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int a = 0; a < AP; ++a) {
+        cplx<R>* dst = slots + (long long)(warp * AP + a) * L;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const int row = lane + 32 * k;
+          if (row < L) dst[row] = A[a][k];
+        }
+      }
+      if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
+      __syncthreads();
+      if (P > 1) {
+        // publish both blocks of this round (block 0 stays in CTA 0)
+        cplx<R>* to = p.xch + (long long)(rnd & 1) * nb * w * L;
+        for (int h = 0; h < 2; ++h) {
+          if (pos[h] == 0) continue;
+          cplx<R>* base = to + (long long)pos[h] * w * L;
+          for (int s = warp; s < w; s += NW) {
+            const cplx<R>* sp = slots + (long long)(h * w + s) * L;
+            cplx<R>* dp = base + (long long)s * L;
+            for (int i = lane; i < L; i += 32) __stcg(dp + i, sp[i]);
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          __threadfence();
+          if (pos[0] != 0) st_release(p.flags + pos[0], rnd + 1);
+          st_release(p.flags + pos[1], rnd + 1);
+        }
+      }
+    }
+    // convergence vote over all CTAs: one counter barrier per sweep
+    if (P > 1) {
+      if (threadIdx.x == 0) {
+        atomicAdd(&p.ctrl->rot[sweep % 3], rot_s);
+        const unsigned old = atom_add_release(&p.ctrl->bar_count, 1u);
+        total_s = (old / (unsigned)P + 1u) * (unsigned)P;   // arrivals that complete this barrier
+      }
+      __syncthreads();
+      if (!cta_wait_geq(&p.ctrl->bar_count, total_s, p.ctrl)) return;
+      if (threadIdx.x == 0) {
+        total_s = ld_acquire(&p.ctrl->rot[sweep % 3]);
+        if (cta == 0) p.ctrl->rot[(sweep + 2) % 3] = 0u;
+      }
+      __syncthreads();
+    } else {
+      if (threadIdx.x == 0) total_s = rot_s;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) rot_total += rot_s;
+    const unsigned total = total_s;
+    __syncthreads();
+    if (total == 0) { converged = true; break; }
+  }
+  // final blocks back to their columns
+  for (int s = warp; s < 2 * w; s += NW) {
+    const int g = gcol[s];
+    if (g < 0) continue;
+    const cplx<R>* src = slots + (long long)s * L;
+    cplx<R>* xd = p.X + (long long)g * p.ldx;
+    for (int i = lane; i < l; i += 32) __stcg(xd + i, src[i]);
+    if (p.W) {
+      cplx<R>* wd = p.W + (long long)g * p.ldw;
+      for (int i = lane; i < p.c; i += 32) __stcg(wd + i, src[l + i]);
+    }
+  }
+  if (threadIdx.x == 0) atomicAdd(&p.ctrl->jac_flops, 24.0 * (double)L * (double)rot_total);
+  if (cta == 0 && threadIdx.x == 0) {
+    const int used = converged ? sweep + 1 : sweep;
+    p.ctrl->sweeps = used;
+    atomicAdd(&p.ctrl->jac_sweeps, (unsigned long long)used);
+    atomicAdd(&p.ctrl->jac_flops, 16.0 * (double)p.l * 0.5 * (double)p.c * (double)(p.c - 1) * (double)used);
+    if (!converged) atomicOr(&p.ctrl->status, ST_NOT_CONVERGED);
+  }
+}
+
+// Kernel variants of the register-resident form, indexed by (warps, rows per lane / 32, columns per warp).
+struct Variant { int nw, rpl, ap; const void* fn; };
+
+#define EAMPS_V(NW, RPL, AP) {NW, RPL, AP, (const void*)jacobi_kernel3<float, NW, RPL, AP>}
+const Variant kVariants[] = {
+    EAMPS_V(4, 4, 1),  EAMPS_V(8, 4, 1),  EAMPS_V(16, 4, 1), EAMPS_V(8, 4, 2),  EAMPS_V(16, 4, 2),
+    EAMPS_V(4, 8, 1),  EAMPS_V(8, 8, 1),  EAMPS_V(16, 8, 1), EAMPS_V(4, 8, 2),  EAMPS_V(8, 8, 2), EAMPS_V(16, 8, 2),
+    EAMPS_V(4, 16, 1), EAMPS_V(8, 16, 1), EAMPS_V(16, 16, 1), EAMPS_V(4, 16, 2), EAMPS_V(8, 16, 2),
+    EAMPS_V(4, 32, 1), EAMPS_V(8, 32, 1),
+};
+#undef EAMPS_V
+
+const Variant* find_variant(int nw, int rpl, int ap) {
+  for (const Variant& v : kVariants)
+    if (v.nw == nw && v.rpl == rpl && v.ap == ap) return &v;
+  return nullptr;
+}
+
 }  // namespace
 
-template <class R> int jacobi_max_ctas(size_t smem) {
+namespace {
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return (v && *v) ? std::atoi(v) : dflt;
+}
+
+int rows_per_lane(int L) {
+  for (int r : {4, 8, 16, 32})
+    if (32 * r >= L) return r;
+  return 0;
+}
+
+}  // namespace
+
+template <class R>
+int jacobi_max_ctas(const JacobiPlan& plan) {
+  const void* fn = plan.fn ? plan.fn : (const void*)jacobi_kernel<R>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem) != cudaSuccess) return 0;
   int per_sm = 0;
-  if (cudaFuncSetAttribute(jacobi_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<R>, 256, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, plan.threads, plan.smem) != cudaSuccess) return 0;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return per_sm * sms;
 }
 
+// Block width, CTA count and kernel variant for one SVD.
+//  * complex64 with columns of at most 1024 rows (accumulated rotations included): the
+//    register-resident kernel; one CTA when every column fits it, else about
+//    c / (2 w) CTAs with w = 8 columns per block (tuning overrides: EAMPS_JACOBI_NW,
+//    EAMPS_JACOBI_AP, EAMPS_JACOBI_SINGLE).
+//  * otherwise (complex128, longer columns): the shared-memory kernel.
 template <class R>
 JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas) {
   JacobiPlan plan;
+  const int L = l + (accumulate ? c : 0);
   const size_t budget = 200 * 1024;
-  const size_t col_bytes = (size_t)(l + (accumulate ? c : 0)) * sizeof(cplx<R>);
+  const size_t col_bytes = (size_t)L * sizeof(cplx<R>);
+  const int rpl = rows_per_lane(L);
+  if (std::is_same<R, float>::value && rpl > 0) {
+    const int target = std::max(1, std::min(sm_count, max_ctas));
+    // single CTA: the widest variant whose columns fit
+    const int single_max = env_int("EAMPS_JACOBI_SINGLE", 64);
+    const Variant* v = nullptr;
+    int w = 0;
+    if (c <= single_max) {
+      const int cand_nw[] = {16, 8, 4};
+      for (int ap : {2, 1}) {
+        for (int nw : cand_nw) {
+          const Variant* cv = find_variant(nw, rpl, ap);
+          if (!cv) continue;
+          const int cw = nw * ap;
+          if (2 * cw >= c && (size_t)2 * cw * col_bytes + 2 * cw * 4 + 16 <= budget) {
+            if (!v || cw < w) { v = cv; w = cw; }   // the narrowest single-CTA variant that holds all columns
+          }
+        }
+      }
+    }
+    int nb = 2;
+    if (!v) {
+      const int nw = env_int("EAMPS_JACOBI_NW", 8), ap = env_int("EAMPS_JACOBI_AP", 1);
+      v = find_variant(nw, rpl, ap);
+      if (!v) v = find_variant(8, rpl, 1);
+      w = v->nw * v->ap;
+      int P = (c + 2 * w - 1) / (2 * w);
+      while (P > target && v) {   // too many CTAs: widen the blocks
+        const Variant* wider = find_variant(v->nw * 2, rpl, v->ap);
+        if (!wider) wider = find_variant(v->nw, rpl, v->ap * 2);
+        if (!wider) break;
+        v = wider;
+        w = v->nw * v->ap;
+        P = (c + 2 * w - 1) / (2 * w);
+      }
+      nb = 2 * P;
+    }
+    const size_t smem = (size_t)2 * w * col_bytes + 2 * w * sizeof(int) + 16;
+    if (v && smem <= 227 * 1024) {
+      plan.w = w;
+      plan.nb = nb;
+      plan.smem = smem;
+      plan.fn = v->fn;
+      plan.threads = v->nw * 32;
+      return plan;
+    }
+  }
+  // shared-memory kernel
   int w_fit = (int)std::max<size_t>(1, budget / (2 * col_bytes + 8));
   int half = (c + 1) / 2;
   if (half <= w_fit && c <= 128) {
-    plan.w = std::max(1, half);        // one CTA holds every column: no grid barrier at all
+    plan.w = std::max(1, half);
     plan.nb = 2;
   } else {
     int target = std::max(1, std::min(sm_count, max_ctas));
     int w = (c + 2 * target - 1) / (2 * target);
     w = std::max(1, std::min(w, w_fit));
     int P = (c + 2 * w - 1) / (2 * w);
-    if (P > target) {  // smem too small for the spread: fall back to the largest fitting block
+    if (P > target) {
       w = w_fit;
       P = (c + 2 * w - 1) / (2 * w);
     }
     plan.w = w;
     plan.nb = 2 * P;
   }
-  plan.smem = (size_t)2 * plan.w * (l + (accumulate ? c : 0)) * sizeof(cplx<R>) + 2 * plan.w * sizeof(int) + 16;
+  plan.smem = (size_t)2 * plan.w * L * sizeof(cplx<R>) + 2 * plan.w * sizeof(int) + 16;
+  plan.fn = (const void*)jacobi_kernel<R>;
+  plan.threads = 256;
   return plan;
 }
 
 template <class R>
 cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int l, int c,
-                          cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cudaStream_t st) {
-  if (c <= 1) {
-    // a single column is already "orthogonal"
-    return cudaSuccess;
-  }
-  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+                          cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cplx<R>* xch,
+                          size_t xch_cap, unsigned* flags, int flags_cap, cudaStream_t st) {
+  if (c <= 1) return cudaSuccess;   // a single column is already orthogonal
+  const size_t L = (size_t)l + (W ? c : 0);
+  if ((size_t)2 * plan.nb * plan.w * L > xch_cap || plan.nb > flags_cap) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(plan.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
   if (e != cudaSuccess) return e;
-  // reset barrier and sweep counters (bar_count, bar_gen, rot[3] are contiguous)
+  // reset barrier and sweep counters (bar_count, bar_gen, rot[3] are contiguous) and the position flags
   e = cudaMemsetAsync(&ctrl->bar_count, 0, 5 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * plan.nb, st);
   if (e != cudaSuccess) return e;
   JArgs<R> a;
   a.X = X; a.ldx = ldx; a.l = l; a.c = c; a.W = W; a.ldw = ldw;
   a.w = plan.w; a.nb = plan.nb; a.max_sweeps = max_sweeps;
   a.tol = R(4) * std::sqrt(R(std::max(l, 1))) * Eps<R>::v;
   a.ctrl = ctrl;
+  a.xch = xch;
+  a.flags = flags;
   void* args[] = {&a};
   const int P = plan.nb / 2;
-  if (P == 1) return cudaLaunchKernel((void*)jacobi_kernel<R>, dim3(1), dim3(256), args, plan.smem, st);
-  return cudaLaunchCooperativeKernel((void*)jacobi_kernel<R>, dim3(P), dim3(256), args, plan.smem, st);
+  if (P == 1) return cudaLaunchKernel(plan.fn, dim3(1), dim3(plan.threads), args, plan.smem, st);
+  return cudaLaunchCooperativeKernel(plan.fn, dim3(P), dim3(plan.threads), args, plan.smem, st);
 }
 
 template JacobiPlan jacobi_plan<float>(int, int, bool, int, int);
 template JacobiPlan jacobi_plan<double>(int, int, bool, int, int);
 template cudaError_t jacobi_launch<float>(const JacobiPlan&, cplx<float>*, long long, int, int, cplx<float>*,
-                                          long long, int, DevCtrl*, cudaStream_t);
+                                          long long, int, DevCtrl*, cplx<float>*, size_t, unsigned*, int,
+                                          cudaStream_t);
 template cudaError_t jacobi_launch<double>(const JacobiPlan&, cplx<double>*, long long, int, int, cplx<double>*,
-                                           long long, int, DevCtrl*, cudaStream_t);
-template int jacobi_max_ctas<float>(size_t);
-template int jacobi_max_ctas<double>(size_t);
+                                           long long, int, DevCtrl*, cplx<double>*, size_t, unsigned*, int,
+                                           cudaStream_t);
+template int jacobi_max_ctas<float>(const JacobiPlan&);
+template int jacobi_max_ctas<double>(const JacobiPlan&);
 
 }  // namespace eamps

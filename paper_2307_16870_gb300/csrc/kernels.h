@@ -14,16 +14,21 @@ namespace eamps {
 // matrix W (column j at W + j*ldw), which must hold the identity on entry, so
 // that W = V.  Cooperative launch; status bits and sweep count go to ctrl.
 struct JacobiPlan {
-  int w = 1;       // columns per block
-  int nb = 2;      // number of blocks (even); CTAs = nb / 2
-  size_t smem = 0; // dynamic shared memory per CTA
+  int w = 1;               // columns per block
+  int nb = 2;              // number of blocks (even); CTAs = nb / 2
+  size_t smem = 0;         // dynamic shared memory per CTA
+  const void* fn = nullptr;  // kernel variant
+  int threads = 256;
 };
 template <class R>
 JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas);
+// xch: exchange slots of the multi-CTA kernels (2 * nb * w * (l + c if W) complex entries at
+// most xch_cap); flags: nb position flags (at most flags_cap).
 template <class R>
 cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int l, int c,
-                          cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cudaStream_t st);
-template <class R> int jacobi_max_ctas(size_t smem);
+                          cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cplx<R>* xch,
+                          size_t xch_cap, unsigned* flags, int flags_cap, cudaStream_t st);
+template <class R> int jacobi_max_ctas(const JacobiPlan& plan);
 
 // ------------------------------------------------------------ CUDA-core GEMM
 // C = alpha * op(A) * op(B); op(A)[i,k] = A[i*a_rs + k*a_cs] (conjugated if conjA).
