@@ -294,7 +294,7 @@ struct Engine final : mps_state {
       if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
     if (c <= 1) return MPS_OK;
     JacobiPlan plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count);
-    const int fit = jacobi_max_ctas<R>(plan);
+    const int fit = plan.cluster > 0 ? plan.cluster : jacobi_max_ctas<R>(plan);
     if (fit <= 0) return MPS_ERR_CUDA;
     if (plan.nb / 2 > fit) {
       plan = jacobi_plan<R>(l, c, acc, sm_count, fit);

@@ -23,6 +23,8 @@
 #include <cstdlib>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace eamps {
@@ -36,6 +38,41 @@ __device__ __forceinline__ int rr_player(int n, int r, int pos) {
 template <class R> struct Eps;
 template <> struct Eps<float> { static constexpr float v = FLT_EPSILON; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
+
+// Parameters of the 2x2 complex Jacobi rotation that makes columns with squared
+// norms a, b and inner product gr + i gi orthogonal; false when the pair is
+// already orthogonal to the tolerance.  FP64: IEEE operations; FP32: fast
+// reciprocal square roots (the rotation only has to be close to unitary).
+template <class R>
+__device__ __forceinline__ bool rot_params(R a, R b, R gr, R gi, R tol, R& cs, R& sn, R& er, R& ei);
+template <>
+__device__ __forceinline__ bool rot_params<double>(double a, double b, double gr, double gi, double tol, double& cs,
+                                                   double& sn, double& er, double& ei) {
+  const double g = sqrt(gr * gr + gi * gi);
+  if (!(a > 0) || !(b > 0) || !(g > tol * sqrt(a) * sqrt(b))) return false;
+  const double zeta = (b - a) / (2 * g);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  cs = 1.0 / sqrt(1.0 + t * t);
+  sn = cs * t;
+  er = gr / g;
+  ei = gi / g;
+  return true;
+}
+template <>
+__device__ __forceinline__ bool rot_params<float>(float a, float b, float gr, float gi, float tol, float& cs,
+                                                  float& sn, float& er, float& ei) {
+  const float g2 = gr * gr + gi * gi;
+  if (!(a > 0.f) || !(b > 0.f) || !(g2 > tol * tol * a * b)) return false;
+  const float rg = rsqrtf(g2);
+  const float zeta = 0.5f * (b - a) * rg;
+  const float z2 = 1.f + zeta * zeta;
+  const float t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + z2 * rsqrtf(z2));
+  cs = rsqrtf(1.f + t * t);
+  sn = cs * t;
+  er = gr * rg;
+  ei = gi * rg;
+  return true;
+}
 
 // Orthogonalise columns x and y (length L, of which the first l enter the
 // inner products).  Returns 1 if a rotation was applied.
@@ -51,13 +88,8 @@ __device__ __forceinline__ int rotate_pair(cplx<R>* __restrict__ x, cplx<R>* __r
     gi = fma(u.x, v.y, fma(-u.y, v.x, gi));
   }
   a = warp_sum(a); b = warp_sum(b); gr = warp_sum(gr); gi = warp_sum(gi);
-  R g = sqrt(gr * gr + gi * gi);
-  if (!(a > 0) || !(b > 0) || !(g > tol * sqrt(a) * sqrt(b))) return 0;
-  R zeta = (b - a) / (2 * g);
-  R t = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-  R cs = R(1) / sqrt(R(1) + t * t);
-  R sn = cs * t;
-  R er = gr / g, ei = gi / g;   // e^{i phi}, phi = arg(a^dagger b)
+  R cs, sn, er, ei;
+  if (!rot_params<R>(a, b, gr, gi, tol, cs, sn, er, ei)) return 0;
   // x' = cs x - sn e^{-i phi} y ;  y' = sn e^{i phi} x + cs y
   for (int i = lane; i < L; i += 32) {
     cplx<R> u = x[i], v = y[i];
@@ -238,6 +270,29 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JArgs<R> p) {
 }
 
 
+// Copy n complex entries global -> shared (or shared -> global) with eight loads in
+// flight per lane; lanes of one warp stride over the column.
+template <class Z, bool kFromGlobal>
+__device__ __forceinline__ void warp_copy(Z* __restrict__ dst, const Z* __restrict__ src, int n, int lane) {
+  constexpr int U = 8;
+  for (int i0 = lane; i0 < n; i0 += 32 * U) {
+    Z v[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int i = i0 + 32 * j;
+      if (i < n) v[j] = kFromGlobal ? __ldcg(src + i) : src[i];
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int i = i0 + 32 * j;
+      if (i < n) {
+        if (kFromGlobal) dst[i] = v[j];
+        else __stcg(dst + i, v[j]);
+      }
+    }
+  }
+}
+
 // Register-resident kernel with point-to-point exchange.  CTA i always holds
 // the positions i (block A) and nb-1-i (block B) of the circle-method
 // tournament; after every round the blocks shift by one position, so each
@@ -277,12 +332,8 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
     const int g = gcol[s];
     cplx<R>* dst = slots + (long long)s * L;
     if (g < 0) { for (int i = lane; i < L; i += 32) dst[i] = mk<R>(0, 0); continue; }
-    const cplx<R>* xs = p.X + (long long)g * p.ldx;
-    for (int i = lane; i < l; i += 32) dst[i] = __ldcg(xs + i);
-    if (p.W) {
-      const cplx<R>* ws = p.W + (long long)g * p.ldw;
-      for (int i = lane; i < p.c; i += 32) dst[l + i] = __ldcg(ws + i);
-    }
+    warp_copy<cplx<R>, true>(dst, p.X + (long long)g * p.ldx, l, lane);
+    if (p.W) warp_copy<cplx<R>, true>(dst + l, p.W + (long long)g * p.ldw, p.c, lane);
   }
   __syncthreads();
 
@@ -297,11 +348,8 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
           const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
           if (!cta_wait_geq(p.flags + src, rnd, p.ctrl)) return;
           const cplx<R>* from = p.xch + ((long long)((rnd - 1) & 1) * nb + src) * w * L;
-          for (int s = warp; s < w; s += NW) {
-            cplx<R>* dst = slots + (long long)(h * w + s) * L;
-            const cplx<R>* sp = from + (long long)s * L;
-            for (int i = lane; i < L; i += 32) dst[i] = __ldcg(sp + i);
-          }
+          for (int s = warp; s < w; s += NW)
+            warp_copy<cplx<R>, true>(slots + (long long)(h * w + s) * L, from + (long long)s * L, L, lane);
         }
         for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
           const int g = rr_player(nb, r, pos[s / w]) * w + (s % w);
@@ -389,14 +437,18 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         }
 #pragma unroll
         for (int a = 0; a < AP; ++a) {
-          const R g = sqrt(gr[a] * gr[a] + gi[a] * gi[a]);
-          const bool rot = val[a] && (da[a] > 0) && (db[a] > 0) && (g > p.tol * sqrt(da[a]) * sqrt(db[a]));
+          // rotation parameters with fast reciprocal square roots: the rotation only has to be
+          // close to unitary (column norms are recomputed from theta afterwards)
+          const float g2 = gr[a] * gr[a] + gi[a] * gi[a];
+          const bool rot = val[a] && (da[a] > 0.f) && (db[a] > 0.f) && (g2 > p.tol * p.tol * da[a] * db[a]);
           if (rot) {
-            const R zeta = (db[a] - da[a]) / (2 * g);
-            const R tt = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-            const R cs = R(1) / sqrt(R(1) + tt * tt);
-            const R sn = cs * tt;
-            const R er = gr[a] / g, ei = gi[a] / g;
+            const float rg = rsqrtf(g2);
+            const float zeta = 0.5f * (db[a] - da[a]) * rg;
+            const float z2 = 1.f + zeta * zeta;
+            const float tt = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + z2 * rsqrtf(z2));
+            const float cs = rsqrtf(1.f + tt * tt);
+            const float sn = cs * tt;
+            const float er = gr[a] * rg, ei = gi[a] * rg;
             cplx<R>* dst = slots + (long long)sb[a] * L;
             // x' = cs x - sn e^{-i phi} y = cs x - al y - be (y.im, -y.re)
             // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al = sn er, be = sn ei
@@ -438,11 +490,8 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         for (int h = 0; h < 2; ++h) {
           if (pos[h] == 0) continue;
           cplx<R>* base = to + (long long)pos[h] * w * L;
-          for (int s = warp; s < w; s += NW) {
-            const cplx<R>* sp = slots + (long long)(h * w + s) * L;
-            cplx<R>* dp = base + (long long)s * L;
-            for (int i = lane; i < L; i += 32) __stcg(dp + i, sp[i]);
-          }
+          for (int s = warp; s < w; s += NW)
+            warp_copy<cplx<R>, false>(base + (long long)s * L, slots + (long long)(h * w + s) * L, L, lane);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -480,12 +529,8 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
     const int g = gcol[s];
     if (g < 0) continue;
     const cplx<R>* src = slots + (long long)s * L;
-    cplx<R>* xd = p.X + (long long)g * p.ldx;
-    for (int i = lane; i < l; i += 32) __stcg(xd + i, src[i]);
-    if (p.W) {
-      cplx<R>* wd = p.W + (long long)g * p.ldw;
-      for (int i = lane; i < p.c; i += 32) __stcg(wd + i, src[l + i]);
-    }
+    warp_copy<cplx<R>, false>(p.X + (long long)g * p.ldx, src, l, lane);
+    if (p.W) warp_copy<cplx<R>, false>(p.W + (long long)g * p.ldw, src + l, p.c, lane);
   }
   if (threadIdx.x == 0) atomicAdd(&p.ctrl->jac_flops, 24.0 * (double)L * (double)rot_total);
   if (cta == 0 && threadIdx.x == 0) {
@@ -495,6 +540,266 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
     atomicAdd(&p.ctrl->jac_flops, 16.0 * (double)p.l * 0.5 * (double)p.c * (double)(p.c - 1) * (double)used);
     if (!converged) atomicOr(&p.ctrl->status, ST_NOT_CONVERGED);
   }
+}
+
+// Cluster-resident kernel: the whole matrix lives in the shared memory of
+// one thread-block cluster (P <= 16 CTAs).  After every round each CTA reads
+// the blocks that shift into its positions straight from its neighbours'
+// shared memory (distributed shared memory) into registers, between two
+// hardware cluster barriers; no global-memory traffic, no flags.  The incoming
+// A columns are already the registers of the next cross phase.
+template <class R, int NW, int RPL, int AP>
+__global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = p.w, nb = p.nb, P = nb / 2;
+  const int L = p.l + (p.W ? p.c : 0);
+  const int l = p.l;
+  cplx<R>* slots = reinterpret_cast<cplx<R>*>(smem_raw);
+  int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * L);
+  __shared__ unsigned rot_s;
+  __shared__ unsigned rot_slot[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cta = (int)cluster.block_rank();
+  const int pos[2] = {cta, nb - 1 - cta};
+  const int wpad = w + (w & 1);
+  unsigned long long rot_total = 0;
+  bool converged = false;
+  int sweep = 0;
+
+  // sources of the blocks that move into my positions: (rank, half) of position src
+  auto holder = [&](int q, int& rank, int& half) {
+    if (q < P) { rank = q; half = 0; } else { rank = nb - 1 - q; half = 1; }
+  };
+  int srank[2], shalf[2];
+  {
+    const int srcA = cta + 1;                              // position cta + 1 (P -> own bottom)
+    holder(srcA, srank[0], shalf[0]);
+    const int srcB = (pos[1] == nb - 1) ? 1 : pos[1] + 1;  // position nb-1 takes from position 1
+    holder(srcB, srank[1], shalf[1]);
+  }
+
+  for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
+    const int g = pos[s / w] * w + (s % w);
+    gcol[s] = g < p.c ? g : -1;
+  }
+  if (threadIdx.x == 0) { rot_slot[0] = 0; rot_slot[1] = 0; }
+  __syncthreads();
+  for (int s = warp; s < 2 * w; s += NW) {
+    const int g = gcol[s];
+    cplx<R>* dst = slots + (long long)s * L;
+    if (g < 0) { for (int i = lane; i < L; i += 32) dst[i] = mk<R>(0, 0); continue; }
+    warp_copy<cplx<R>, true>(dst, p.X + (long long)g * p.ldx, l, lane);
+    if (p.W) warp_copy<cplx<R>, true>(dst + l, p.W + (long long)g * p.ldw, p.c, lane);
+  }
+  __syncthreads();
+
+  for (sweep = 0; sweep < p.max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rot_s = 0;
+    __syncthreads();
+    for (int r = 0; r < nb - 1; ++r) {
+      unsigned my_rot = 0;
+      if (r == 0) {
+        const int half = wpad / 2;
+        for (int t = 0; t < wpad - 1; ++t) {
+          for (int pi = warp; pi < 2 * half; pi += NW) {
+            const int blk = pi / half, i = pi % half;
+            int s1 = rr_player(wpad, t, i), s2 = rr_player(wpad, t, wpad - 1 - i);
+            if (s1 >= w || s2 >= w) continue;
+            s1 += blk * w; s2 += blk * w;
+            if (gcol[s1] < 0 || gcol[s2] < 0) continue;
+            my_rot += rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, l, L, p.tol, lane);
+          }
+          __syncthreads();
+        }
+      }
+      cplx<R> A[AP][RPL], B[AP][RPL];
+#pragma unroll
+      for (int a = 0; a < AP; ++a) {
+        const cplx<R>* src = slots + (long long)(warp * AP + a) * L;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const int row = lane + 32 * k;
+          A[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
+        }
+      }
+      for (int t = 0; t < w; ++t) {
+        int sb[AP];
+        bool val[AP];
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          const int ia = warp * AP + a;
+          sb[a] = w + (ia + t) % w;
+          val[a] = gcol[ia] >= 0 && gcol[sb[a]] >= 0;
+          const cplx<R>* src = slots + (long long)sb[a] * L;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const int row = lane + 32 * k;
+            B[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
+          }
+        }
+        float2 d2a[AP], d2b[AP], g2a[AP], g2b[AP];
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          d2a[a] = make_float2(0.f, 0.f); d2b[a] = d2a[a]; g2a[a] = d2a[a]; g2b[a] = d2a[a];
+        }
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          if (lane + 32 * k < l) {
+#pragma unroll
+            for (int a = 0; a < AP; ++a) {
+              const float2 u = A[a][k], v = B[a][k];
+              d2a[a] = __ffma2_rn(u, u, d2a[a]);
+              d2b[a] = __ffma2_rn(v, v, d2b[a]);
+              g2a[a] = __ffma2_rn(u, v, g2a[a]);
+              g2b[a] = __ffma2_rn(u, make_float2(v.y, v.x), g2b[a]);
+            }
+          }
+        }
+        float da[AP], db[AP], gr[AP], gi[AP];
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          da[a] = d2a[a].x + d2a[a].y; db[a] = d2b[a].x + d2b[a].y;
+          gr[a] = g2a[a].x + g2a[a].y; gi[a] = g2b[a].x - g2b[a].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int a = 0; a < AP; ++a) {
+            da[a] += __shfl_xor_sync(0xffffffffu, da[a], o);
+            db[a] += __shfl_xor_sync(0xffffffffu, db[a], o);
+            gr[a] += __shfl_xor_sync(0xffffffffu, gr[a], o);
+            gi[a] += __shfl_xor_sync(0xffffffffu, gi[a], o);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          float cs, sn, er, ei;
+          if (val[a] && rot_params<float>(da[a], db[a], gr[a], gi[a], p.tol, cs, sn, er, ei)) {
+            cplx<R>* dst = slots + (long long)sb[a] * L;
+            const float al = sn * er, be = sn * ei;
+            const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
+            const float2 pbe = make_float2(-be, be);
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const float2 u = A[a][k], v = B[a][k];
+              float2 nu = __fmul2_rn(u, csv);
+              nu = __ffma2_rn(v, mal, nu);
+              nu = __ffma2_rn(make_float2(v.y, v.x), pbe, nu);
+              float2 nv = __fmul2_rn(v, csv);
+              nv = __ffma2_rn(u, pal, nv);
+              nv = __ffma2_rn(make_float2(u.y, u.x), pbe, nv);
+              A[a][k] = nu;
+              const int row = lane + 32 * k;
+              if (row < L) dst[row] = nv;
+            }
+            ++my_rot;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int a = 0; a < AP; ++a) {
+        cplx<R>* dst = slots + (long long)(warp * AP + a) * L;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const int row = lane + 32 * k;
+          if (row < L) dst[row] = A[a][k];
+        }
+      }
+      if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
+      __syncthreads();
+      const bool last = (r == nb - 2);
+      if (last && threadIdx.x == 0) rot_slot[sweep & 1] = rot_s;
+      if (P > 1) {
+        cluster.sync();   // every CTA finished the round: its shared blocks are final
+        // Two phases, one block staged in registers at a time.  Phase 1: CTAs 1..P-1 take the
+        // block for their A half (position i+1), CTA 0 takes position 1's block for its B half
+        // and keeps it in registers to the end (its own B half is still read in phase 2).
+        // Phase 2: CTAs 1..P-1 take the block for their B half (position nb-i).
+        cplx<R> in[AP][RPL];
+        {
+          const int rk = (cta == 0) ? srank[1] : srank[0];
+          const int hf = (cta == 0) ? shalf[1] : shalf[0];
+          const cplx<R>* remote = cluster.map_shared_rank(slots, rk);
+#pragma unroll
+          for (int a = 0; a < AP; ++a) {
+            const cplx<R>* src = remote + (long long)(hf * w + warp * AP + a) * L;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const int row = lane + 32 * k;
+              in[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
+            }
+          }
+        }
+        unsigned vote = 0;
+        if (last && threadIdx.x == 0) {
+          for (int q = 0; q < P; ++q) vote += cluster.map_shared_rank(rot_slot, q)[sweep & 1];
+        }
+        cluster.sync();   // phase-1 sources read
+        if (cta != 0) {
+#pragma unroll
+          for (int a = 0; a < AP; ++a) {
+            cplx<R>* dst = slots + (long long)(warp * AP + a) * L;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const int row = lane + 32 * k;
+              if (row < L) dst[row] = in[a][k];
+            }
+          }
+          const cplx<R>* remote = cluster.map_shared_rank(slots, srank[1]);
+#pragma unroll
+          for (int a = 0; a < AP; ++a) {
+            const cplx<R>* src = remote + (long long)(shalf[1] * w + warp * AP + a) * L;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+              const int row = lane + 32 * k;
+              in[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
+            }
+          }
+        }
+        cluster.sync();   // phase-2 sources read
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          cplx<R>* dst = slots + (long long)(w + warp * AP + a) * L;
+#pragma unroll
+          for (int k = 0; k < RPL; ++k) {
+            const int row = lane + 32 * k;
+            if (row < L) dst[row] = in[a][k];
+          }
+        }
+        const int rn = last ? 0 : r + 1;
+        for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
+          const int g = rr_player(nb, rn, pos[s / w]) * w + (s % w);
+          gcol[s] = g < p.c ? g : -1;
+        }
+        if (last && threadIdx.x == 0) rot_s = vote;
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) rot_total += (P > 1) ? rot_slot[sweep & 1] : rot_s;
+    const unsigned total = rot_s;   // P > 1: the cluster-wide vote; P == 1: this CTA's count
+    __syncthreads();
+    if (total == 0) { converged = true; break; }
+  }
+  // final blocks back to their columns
+  for (int s = warp; s < 2 * w; s += NW) {
+    const int g = gcol[s];
+    if (g < 0) continue;
+    const cplx<R>* src = slots + (long long)s * L;
+    warp_copy<cplx<R>, false>(p.X + (long long)g * p.ldx, src, l, lane);
+    if (p.W) warp_copy<cplx<R>, false>(p.W + (long long)g * p.ldw, src + l, p.c, lane);
+  }
+  if (threadIdx.x == 0) atomicAdd(&p.ctrl->jac_flops, 24.0 * (double)L * (double)rot_total);
+  if (cta == 0 && threadIdx.x == 0) {
+    const int used = converged ? sweep + 1 : sweep;
+    p.ctrl->sweeps = used;
+    atomicAdd(&p.ctrl->jac_sweeps, (unsigned long long)used);
+    atomicAdd(&p.ctrl->jac_flops, 16.0 * (double)p.l * 0.5 * (double)p.c * (double)(p.c - 1) * (double)used);
+    if (!converged) atomicOr(&p.ctrl->status, ST_NOT_CONVERGED);
+  }
+  cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 // Kernel variants of the register-resident form, indexed by (warps, rows per lane / 32, columns per warp).
@@ -508,6 +813,18 @@ const Variant kVariants[] = {
     EAMPS_V(4, 32, 1), EAMPS_V(8, 32, 1),
 };
 #undef EAMPS_V
+
+#define EAMPS_C(NW, RPL) {NW, RPL, 1, (const void*)jacobi_cluster_kernel<float, NW, RPL, 1>}
+const Variant kClusterVariants[] = {
+    EAMPS_C(8, 4), EAMPS_C(16, 4), EAMPS_C(8, 8), EAMPS_C(16, 8), EAMPS_C(8, 16), EAMPS_C(16, 16),
+};
+#undef EAMPS_C
+
+const Variant* find_cluster_variant(int nw, int rpl) {
+  for (const Variant& v : kClusterVariants)
+    if (v.nw == nw && v.rpl == rpl) return &v;
+  return nullptr;
+}
 
 const Variant* find_variant(int nw, int rpl, int ap) {
   for (const Variant& v : kVariants)
@@ -557,6 +874,27 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
   const size_t budget = 200 * 1024;
   const size_t col_bytes = (size_t)L * sizeof(cplx<R>);
   const int rpl = rows_per_lane(L);
+  if (std::is_same<R, float>::value && rpl > 0 && rpl <= 16 && env_int("EAMPS_JACOBI_CLUSTER", 1)) {
+    // whole matrix in one cluster of at most 16 CTAs with 8 warps each (w = 8), i.e. up to 256
+    // columns; wider blocks (16 warps) were measured slower than the point-to-point kernel on
+    // more SMs, because a step's latency grows with the warps that share an SM
+    const int nw = env_int("EAMPS_JACOBI_CNW", 8);
+    const Variant* v = find_cluster_variant(nw, rpl);
+    if (v) {
+      const int w = v->nw;
+      const int P = (c + 2 * w - 1) / (2 * w);
+      const size_t smem = (size_t)2 * w * col_bytes + 2 * w * sizeof(int) + 16;
+      if (P >= 2 && P <= 16 && smem <= 200 * 1024) {
+        plan.w = w;
+        plan.nb = 2 * P;
+        plan.smem = smem;
+        plan.fn = v->fn;
+        plan.threads = v->nw * 32;
+        plan.cluster = P;
+        return plan;
+      }
+    }
+  }
   if (std::is_same<R, float>::value && rpl > 0) {
     const int target = std::max(1, std::min(sm_count, max_ctas));
     // single CTA: the widest variant whose columns fit
@@ -650,6 +988,25 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
   a.flags = flags;
   void* args[] = {&a};
   const int P = plan.nb / 2;
+  if (plan.cluster > 0) {
+    if (plan.cluster > 8) {
+      e = cudaFuncSetAttribute(plan.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, plan.fn, args);
+  }
   if (P == 1) return cudaLaunchKernel(plan.fn, dim3(1), dim3(plan.threads), args, plan.smem, st);
   return cudaLaunchCooperativeKernel(plan.fn, dim3(P), dim3(plan.threads), args, plan.smem, st);
 }

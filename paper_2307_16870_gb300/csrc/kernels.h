@@ -19,6 +19,7 @@ struct JacobiPlan {
   size_t smem = 0;         // dynamic shared memory per CTA
   const void* fn = nullptr;  // kernel variant
   int threads = 256;
+  int cluster = 0;           // > 0: cluster-resident kernel, one cluster of this many CTAs
 };
 template <class R>
 JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas);
