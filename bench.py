@@ -59,6 +59,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    ap.add_argument("--micro", type=int, default=0, metavar="CHI",
+                    help="instead of the circuit: a few two-site updates on a random canonical 24-site MPS "
+                         "with every bond CHI (the launch configuration of the circuit's saturated gates)")
     return ap.parse_args(argv)
 
 
@@ -321,8 +324,33 @@ def run_ours(a) -> int:
     return 0
 
 
+def run_micro(a) -> int:
+    """Per-launch Jacobi timing of saturated updates (used for focused profiling)."""
+    import torch
+    import paper_2307_16870_gb300 as E
+    prec = {"tf32x3": E.TF32X3, "fp32": E.FP32, "fp64": E.FP64}[a.precision]
+    chi, n = a.micro, 24
+    q = n // 2
+    sites, _ = W.random_canonical_mps(n, chi, q, seed=7)
+    m = E.MPS(n, chi_max=chi, fixed_chi=chi, precision=prec, log_truncations=False)
+    m.load_sites(sites, q)
+    m.profile(True)
+    for g in range(max(a.steps, 1) + 1):
+        m.apply_2q(q, W.haar_unitary(4, 3, g), 1.0)
+    torch.cuda.synchronize()
+    st = m.stats()
+    jl = max(st["jacobi_launches"], 1)
+    print(json.dumps({"micro_chi": chi, "jacobi_ms_per_launch": st["jacobi_ms"] / jl,
+                      "sweeps_per_launch": st["jacobi_sweeps"] / jl,
+                      "jacobi_tflops": st["jacobi_flops"] / (st["jacobi_ms"] / 1e3) / 1e12 if st["jacobi_ms"] else None}))
+    m.close()
+    return 0
+
+
 def main(argv=None) -> int:
     a = parse_args(argv)
+    if a.micro:
+        return run_micro(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

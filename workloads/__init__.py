@@ -47,6 +47,7 @@ __all__ = [
     "amplitude_damping_kraus",
     "random_batch_specs",
     "count_brickwork_gates",
+    "random_canonical_mps",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -212,3 +213,35 @@ def random_batch_specs(count: int, seed: int, n_range=(20, 80), depth_range=(10,
         f = f_choices[int(u[i, 2] * len(f_choices))]
         specs.append({"n_qubits": n, "depth": d, "f_min": f, "seed": seed * 1000 + i + 1})
     return specs
+
+
+def random_canonical_mps(n, chi_cap, centre, seed, d=2, round_c64=True):
+    """Random MPS in canonical form around ``centre`` (synthetic input state).
+
+    Sites left of the centre are random left isometries, sites right of it
+    random right isometries (both from the QR of complex Ginibre matrices),
+    the centre a random unit tensor; bonds are min(chi_cap, d^min(b, n-b)).
+    With ``round_c64`` every entry is first rounded to complex64, so that a
+    complex64 copy holds exactly the same numbers.  Returns (sites, bonds).
+    """
+    bonds = [1] + [min(chi_cap, d ** min(b, n - b)) for b in range(1, n)] + [1]
+    sites = []
+    off = 0
+    for i in range(n):
+        cl, cr = bonds[i], bonds[i + 1]
+        cnt = cl * d * cr
+        g = normals(seed, off, 2 * cnt).reshape(2, cnt)
+        off += 2 * cnt + 2
+        t = (g[0] + 1j * g[1]).reshape(cl, d, cr)
+        if i < centre:
+            q, _ = np.linalg.qr(t.reshape(cl * d, cr))
+            t = q.reshape(cl, d, cr)
+        elif i > centre:
+            q, _ = np.linalg.qr(t.reshape(cl, d * cr).conj().T)
+            t = q.conj().T.reshape(cl, d, cr)
+        else:
+            t = t / np.linalg.norm(t)
+        if round_c64:
+            t = t.astype(np.complex64).astype(np.complex128)
+        sites.append(np.ascontiguousarray(t))
+    return sites, bonds
