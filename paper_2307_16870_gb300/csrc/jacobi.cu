@@ -145,6 +145,59 @@ __device__ __forceinline__ bool cta_wait_geq(const unsigned* a, unsigned target,
   return ok_s != 0;
 }
 
+// Thread 0 only: bounded spin until *a >= target (sets ST_TIMEOUT and returns false on expiry).
+__device__ __forceinline__ bool spin_geq(const unsigned* a, unsigned target, DevCtrl* ctrl) {
+  long long spins = 0;
+  while (ld_acquire(a) < target) {
+    if (++spins > 64) __nanosleep(20);
+    if (spins > kSpinLimit || (*(volatile int*)&ctrl->status & ST_TIMEOUT)) {
+      atomicOr(&ctrl->status, ST_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bulk (TMA, untiled) copies between the exchange slots and shared memory.  Both
+// addresses are 16-byte aligned and the size is a multiple of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void xbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  // make the initialised barrier visible to the async proxy that completes the copies
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void xbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void xbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Bounded wait for the phase of the given parity; false on expiry.
+__device__ __forceinline__ bool xbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store_drain() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 template <class R>
 __device__ void load_pair(const JArgs<R>& p, cplx<R>* slots, int* gcol, int L, int bA, int bB) {
   const int w = p.w;
@@ -303,6 +356,11 @@ __device__ __forceinline__ void warp_copy(Z* __restrict__ dst, const Z* __restri
 // so it cannot finish two rounds before that reader has taken the block.  The
 // only grid-wide synchronisation is one counter barrier per sweep for the
 // convergence vote.
+//
+// Blocks move by bulk copies (one per block and direction) when a block is a
+// whole number of 16-byte units: the publishing thread drains its stores
+// before the release, and the reading thread orders its bulk load after the
+// acquire with a proxy fence.
 template <class R, int NW, int RPL, int AP>
 __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -316,6 +374,14 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cta = blockIdx.x;
   const int pos[2] = {cta, nb - 1 - cta};
+  __shared__ __align__(8) uint64_t xbar;   // completion of the incoming bulk copies
+  __shared__ int xok_s;
+  const long long blk = (long long)w * L;   // entries per block
+  const bool bulk = P > 1 && (blk * (long long)sizeof(cplx<R>)) % 16 == 0 &&
+                    (reinterpret_cast<uintptr_t>(p.xch) & 15) == 0 && blk * (long long)sizeof(cplx<R>) < (1 << 19);
+  const uint32_t blk_bytes = (uint32_t)(blk * (long long)sizeof(cplx<R>));
+  uint32_t xphase = 0;
+  if (bulk && threadIdx.x == 0) xbar_init(&xbar);
   const int wpad = w + (w & 1);
   unsigned long long rot_total = 0;
   bool converged = false;
@@ -343,13 +409,37 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
     for (int r = 0; r < nb - 1; ++r, ++rnd) {
       if (rnd > 0 && P > 1) {
         // take the blocks that moved into my positions
-        for (int h = 0; h < 2; ++h) {
-          if (pos[h] == 0) continue;                      // block 0 never moves
-          const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
-          if (!cta_wait_geq(p.flags + src, rnd, p.ctrl)) return;
-          const cplx<R>* from = p.xch + ((long long)((rnd - 1) & 1) * nb + src) * w * L;
-          for (int s = warp; s < w; s += NW)
-            warp_copy<cplx<R>, true>(slots + (long long)(h * w + s) * L, from + (long long)s * L, L, lane);
+        if (bulk) {
+          if (threadIdx.x == 0) {
+            int ok = 1;
+            for (int h = 0; h < 2 && ok; ++h) {
+              if (pos[h] == 0) continue;                  // block 0 never moves
+              const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
+              if (!spin_geq(p.flags + src, rnd, p.ctrl)) { ok = 0; break; }
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              xbar_expect(&xbar, blk_bytes);
+              bulk_load(slots + h * blk, p.xch + ((long long)((rnd - 1) & 1) * nb + src) * blk, blk_bytes, &xbar);
+            }
+            xbar_arrive(&xbar);   // the phase completes when the issued copies have landed
+            xok_s = ok;
+          }
+          const bool landed = xbar_wait(&xbar, xphase);
+          xphase ^= 1u;
+          if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(&p.ctrl->status, ST_TIMEOUT);
+            xbar_wait(&xbar, xphase ^ 1u);   // let copies in flight land before the CTA exits
+            return;
+          }
+          if (!xok_s) return;
+        } else {
+          for (int h = 0; h < 2; ++h) {
+            if (pos[h] == 0) continue;                    // block 0 never moves
+            const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
+            if (!cta_wait_geq(p.flags + src, rnd, p.ctrl)) return;
+            const cplx<R>* from = p.xch + ((long long)((rnd - 1) & 1) * nb + src) * blk;
+            for (int s = warp; s < w; s += NW)
+              warp_copy<cplx<R>, true>(slots + (long long)(h * w + s) * L, from + (long long)s * L, L, lane);
+          }
         }
         for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
           const int g = rr_player(nb, r, pos[s / w]) * w + (s % w);
@@ -483,21 +573,35 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         }
       }
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
+      // shared-memory writes above must be visible to the bulk stores below
+      if (bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (P > 1) {
         // publish both blocks of this round (block 0 stays in CTA 0)
-        cplx<R>* to = p.xch + (long long)(rnd & 1) * nb * w * L;
-        for (int h = 0; h < 2; ++h) {
-          if (pos[h] == 0) continue;
-          cplx<R>* base = to + (long long)pos[h] * w * L;
-          for (int s = warp; s < w; s += NW)
-            warp_copy<cplx<R>, false>(base + (long long)s * L, slots + (long long)(h * w + s) * L, L, lane);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          __threadfence();
-          if (pos[0] != 0) st_release(p.flags + pos[0], rnd + 1);
-          st_release(p.flags + pos[1], rnd + 1);
+        cplx<R>* to = p.xch + (long long)(rnd & 1) * nb * blk;
+        if (bulk) {
+          if (threadIdx.x == 0) {
+            for (int h = 0; h < 2; ++h)
+              if (pos[h] != 0) bulk_store(to + (long long)pos[h] * blk, slots + h * blk, blk_bytes);
+            bulk_store_drain();   // also ends the reads of shared memory before the next loads
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __threadfence();
+            if (pos[0] != 0) st_release(p.flags + pos[0], rnd + 1);
+            st_release(p.flags + pos[1], rnd + 1);
+          }
+        } else {
+          for (int h = 0; h < 2; ++h) {
+            if (pos[h] == 0) continue;
+            cplx<R>* base = to + (long long)pos[h] * blk;
+            for (int s = warp; s < w; s += NW)
+              warp_copy<cplx<R>, false>(base + (long long)s * L, slots + (long long)(h * w + s) * L, L, lane);
+          }
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            __threadfence();
+            if (pos[0] != 0) st_release(p.flags + pos[0], rnd + 1);
+            st_release(p.flags + pos[1], rnd + 1);
+          }
         }
       }
     }
