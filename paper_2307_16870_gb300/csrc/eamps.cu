@@ -223,9 +223,10 @@ struct Engine final : mps_state {
         !dalloc(&wdev, (size_t)N * d) || !dalloc(&w2dev, 16) || !dalloc(&work, (size_t)(2 + d) * (chi_cap + 8)) ||
         !dalloc(&outdev, 4) || !dalloc(&stage, site_max))
       return MPS_ERR_OOM;
-    // exchange slots: 2 parities x (columns + padding of one block per CTA) x column length,
-    // column length at most the longer side plus accumulated rotations
-    xch_cap = (size_t)2 * ((size_t)c_max + 2 * 64) * (size_t)(2 * c_max);
+    // exchange slots: 2 parities x (columns + padding of one block per CTA) x column stride; the
+    // stride is the longer side plus accumulated rotations, padded to 32 * (rows per lane) <= 1024
+    // rows by the register-resident kernels
+    xch_cap = (size_t)2 * ((size_t)c_max + 2 * 64) * (size_t)std::max(1024, 2 * c_max + 32);
     if (!dalloc(&xch, xch_cap) || !dalloc(&jflags, kFlagsCap)) return MPS_ERR_OOM;
     site_cap = site_max;
     if (cudaMallocHost((void**)&hctrl, sizeof(DevCtrl)) != cudaSuccess) return MPS_ERR_OOM;

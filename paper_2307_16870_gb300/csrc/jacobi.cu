@@ -346,6 +346,180 @@ __device__ __forceinline__ void warp_copy(Z* __restrict__ dst, const Z* __restri
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident kernels (complex64).
+//
+// Column layout in shared memory and in the exchange slots: ld = 32 * RPL rows,
+// zero padded.  Rows [0, l) hold the column of X; when the rotations are
+// accumulated, rows [lw, lw + c) hold the column of W, lw = l rounded up to a
+// multiple of 32; every other row is zero.  Zero rows stay zero under the
+// rotations, so loads and stores need no per-row bounds test, and the inner
+// products run over the first kl = lw / 32 rows of each lane (all RPL rows
+// when nothing is accumulated).  Columns past c are zero too: their squared
+// norm is zero, so the rotation test skips every pair they are in.
+
+// Column g of X (and of W) into a padded slot column; g < 0: a zero column.
+template <int RPL>
+__device__ __forceinline__ void fill_column(float2* __restrict__ dst, const JArgs<float>& p, int g, int lw, int lane) {
+  constexpr int ld = 32 * RPL;
+  if (g < 0) {
+    for (int i = lane; i < ld; i += 32) dst[i] = make_float2(0.f, 0.f);
+    return;
+  }
+  warp_copy<float2, true>(dst, p.X + (long long)g * p.ldx, p.l, lane);
+  const int wend = p.W ? lw + p.c : p.l;
+  for (int i = p.l + lane; i < lw && p.W; i += 32) dst[i] = make_float2(0.f, 0.f);
+  if (p.W) warp_copy<float2, true>(dst + lw, p.W + (long long)g * p.ldw, p.c, lane);
+  for (int i = wend + lane; i < ld; i += 32) dst[i] = make_float2(0.f, 0.f);
+}
+
+// Padded slot column back to column g of X (and of W).
+__device__ __forceinline__ void drain_column(const float2* __restrict__ src, const JArgs<float>& p, int g, int lw,
+                                             int lane) {
+  if (g < 0) return;
+  warp_copy<float2, false>(p.X + (long long)g * p.ldx, src, p.l, lane);
+  if (p.W) warp_copy<float2, false>(p.W + (long long)g * p.ldw, src + lw, p.c, lane);
+}
+
+// Sum of each of N = 4 or 8 values over the 32 lanes of a warp, returned in every lane.
+// Reduce-scatter (each halving level sends half of the remaining values), a butterfly on
+// the single value left, then a broadcast: 2N - 1 + 5 - log2 N shuffles instead of 5 N.
+template <int N>
+__device__ __forceinline__ void warp_allreduce(float (&v)[N], int lane) {
+  static_assert(N == 4 || N == 8, "four or eight values");
+  constexpr int LOG = (N == 4) ? 2 : 3;
+  float cur[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) cur[i] = v[i];
+#pragma unroll
+  for (int lev = 0; lev < LOG; ++lev) {
+    const int half = (N >> lev) / 2;
+    const int o = 16 >> lev;
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = upper ? cur[i] : cur[i + half];
+      const float keep = upper ? cur[i + half] : cur[i];
+      cur[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int o = 16 >> LOG; o > 0; o >>= 1) cur[0] += __shfl_xor_sync(0xffffffffu, cur[0], o);
+  // lane holds the sum of value (lane >> (5 - LOG))
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = __shfl_sync(0xffffffffu, cur[0], i << (5 - LOG));
+}
+
+// The w*w cross pairs of one round.  Warp `warp` keeps A columns ia = warp*AP + a in
+// registers; at step t it takes B column w + (ia + t) mod w, which warp + 1 (mod NW)
+// released at step t - 1.  Returns the rotations applied by this warp.
+template <int NW, int RPL, int AP>
+__device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int w, int kl, float tol, int lane,
+                                                int warp) {
+  constexpr int ld = 32 * RPL;
+  float2 A[AP][RPL], B[AP][RPL];
+  int ib[AP];
+#pragma unroll
+  for (int a = 0; a < AP; ++a) {
+    ib[a] = warp * AP + a;
+    const float2* src = slots + ib[a] * ld + lane;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) A[a][k] = src[32 * k];
+  }
+  unsigned my_rot = 0;
+  for (int t = 0; t < w; ++t) {
+    float2* bcol[AP];
+#pragma unroll
+    for (int a = 0; a < AP; ++a) {
+      bcol[a] = slots + (w + ib[a]) * ld + lane;
+#pragma unroll
+      for (int k = 0; k < RPL; ++k) B[a][k] = bcol[a][32 * k];
+    }
+    // packed two-wide FP32: (u.re*u.re, u.im*u.im) style partial sums
+    float2 d2a[AP], d2b[AP], g2a[AP], g2b[AP];
+#pragma unroll
+    for (int a = 0; a < AP; ++a) {
+      d2a[a] = make_float2(0.f, 0.f); d2b[a] = d2a[a]; g2a[a] = d2a[a]; g2b[a] = d2a[a];
+    }
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      if (k < kl) {
+#pragma unroll
+        for (int a = 0; a < AP; ++a) {
+          const float2 u = A[a][k], v = B[a][k];
+          d2a[a] = __ffma2_rn(u, u, d2a[a]);
+          d2b[a] = __ffma2_rn(v, v, d2b[a]);
+          g2a[a] = __ffma2_rn(u, v, g2a[a]);                         // (u.re v.re, u.im v.im)
+          g2b[a] = __ffma2_rn(u, make_float2(v.y, v.x), g2b[a]);      // (u.re v.im, u.im v.re)
+        }
+      }
+    }
+    float s[4 * AP];
+#pragma unroll
+    for (int a = 0; a < AP; ++a) {
+      s[4 * a + 0] = d2a[a].x + d2a[a].y;
+      s[4 * a + 1] = d2b[a].x + d2b[a].y;
+      s[4 * a + 2] = g2a[a].x + g2a[a].y;      // Re(u^dagger v)
+      s[4 * a + 3] = g2b[a].x - g2b[a].y;      // Im(u^dagger v)
+    }
+    warp_allreduce<4 * AP>(s, lane);
+#pragma unroll
+    for (int a = 0; a < AP; ++a) {
+      float cs, sn, er, ei;
+      if (rot_params<float>(s[4 * a], s[4 * a + 1], s[4 * a + 2], s[4 * a + 3], tol, cs, sn, er, ei)) {
+        // x' = cs x - sn e^{-i phi} y = cs x - al y - be (y.im, -y.re)
+        // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al = sn er, be = sn ei
+        const float al = sn * er, be = sn * ei;
+        const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
+        const float2 pbe = make_float2(-be, be);
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const float2 u = A[a][k], v = B[a][k];
+          float2 nu = __fmul2_rn(u, csv);
+          nu = __ffma2_rn(v, mal, nu);
+          nu = __ffma2_rn(make_float2(v.y, v.x), pbe, nu);
+          float2 nv = __fmul2_rn(v, csv);
+          nv = __ffma2_rn(u, pal, nv);
+          nv = __ffma2_rn(make_float2(u.y, u.x), pbe, nv);
+          A[a][k] = nu;
+          bcol[a][32 * k] = nv;
+        }
+        ++my_rot;
+      }
+      ib[a] = (ib[a] + 1 == w) ? 0 : ib[a] + 1;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < AP; ++a) {
+    float2* dst = slots + (warp * AP + a) * ld + lane;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) dst[32 * k] = A[a][k];
+  }
+  return my_rot;
+}
+
+// Pairs inside each of the two blocks (round 0 of a sweep): round robin over wpad players,
+// both blocks at once, one warp per pair.
+__device__ __forceinline__ unsigned intra_phase(float2* slots, const int* gcol, int w, int ld, int lrows, float tol,
+                                                int lane, int warp, int nwarps) {
+  const int wpad = w + (w & 1);
+  const int half = wpad / 2;
+  unsigned my_rot = 0;
+  for (int t = 0; t < wpad - 1; ++t) {
+    for (int pi = warp; pi < 2 * half; pi += nwarps) {
+      const int blk = pi / half, i = pi % half;
+      int s1 = rr_player(wpad, t, i), s2 = rr_player(wpad, t, wpad - 1 - i);
+      if (s1 >= w || s2 >= w) continue;
+      s1 += blk * w; s2 += blk * w;
+      if (gcol[s1] < 0 || gcol[s2] < 0) continue;
+      my_rot += rotate_pair<float>(slots + (long long)s1 * ld, slots + (long long)s2 * ld, lrows, ld, tol, lane);
+    }
+    __syncthreads();
+  }
+  return my_rot;
+}
+
 // Register-resident kernel with point-to-point exchange.  CTA i always holds
 // the positions i (block A) and nb-1-i (block B) of the circle-method
 // tournament; after every round the blocks shift by one position, so each
@@ -357,32 +531,31 @@ __device__ __forceinline__ void warp_copy(Z* __restrict__ dst, const Z* __restri
 // only grid-wide synchronisation is one counter barrier per sweep for the
 // convergence vote.
 //
-// Blocks move by bulk copies (one per block and direction) when a block is a
-// whole number of 16-byte units: the publishing thread drains its stores
-// before the release, and the reading thread orders its bulk load after the
-// acquire with a proxy fence.
+// Blocks move by bulk copies (one per block and direction): the publishing
+// thread drains its stores before the release, and the reading thread orders
+// its bulk load after the acquire with a proxy fence.
 template <class R, int NW, int RPL, int AP>
 __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
+  static_assert(std::is_same<R, float>::value, "register-resident kernels are complex64");
+  constexpr int ld = 32 * RPL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = p.w, nb = p.nb, P = nb / 2;
-  const int L = p.l + (p.W ? p.c : 0);
-  const int l = p.l;
-  cplx<R>* slots = reinterpret_cast<cplx<R>*>(smem_raw);
-  int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * L);
+  const int lw = (p.l + 31) & ~31;
+  const int kl = p.W ? lw / 32 : RPL;
+  float2* slots = reinterpret_cast<float2*>(smem_raw);
+  int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * ld);
   __shared__ unsigned rot_s;
   __shared__ unsigned total_s;
+  __shared__ __align__(8) uint64_t xbar;   // completion of the incoming bulk copies
+  __shared__ int xok_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cta = blockIdx.x;
   const int pos[2] = {cta, nb - 1 - cta};
-  __shared__ __align__(8) uint64_t xbar;   // completion of the incoming bulk copies
-  __shared__ int xok_s;
-  const long long blk = (long long)w * L;   // entries per block
-  const bool bulk = P > 1 && (blk * (long long)sizeof(cplx<R>)) % 16 == 0 &&
-                    (reinterpret_cast<uintptr_t>(p.xch) & 15) == 0 && blk * (long long)sizeof(cplx<R>) < (1 << 19);
-  const uint32_t blk_bytes = (uint32_t)(blk * (long long)sizeof(cplx<R>));
+  const long long blk = (long long)w * ld;   // entries per block
+  const uint32_t blk_bytes = (uint32_t)(blk * (long long)sizeof(float2));
+  const bool bulk = P > 1 && (reinterpret_cast<uintptr_t>(p.xch) & 15) == 0 && blk_bytes < (1u << 19);
   uint32_t xphase = 0;
   if (bulk && threadIdx.x == 0) xbar_init(&xbar);
-  const int wpad = w + (w & 1);
   unsigned long long rot_total = 0;
   bool converged = false;
   int sweep = 0;
@@ -394,13 +567,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
     gcol[s] = g < p.c ? g : -1;
   }
   __syncthreads();
-  for (int s = warp; s < 2 * w; s += NW) {
-    const int g = gcol[s];
-    cplx<R>* dst = slots + (long long)s * L;
-    if (g < 0) { for (int i = lane; i < L; i += 32) dst[i] = mk<R>(0, 0); continue; }
-    warp_copy<cplx<R>, true>(dst, p.X + (long long)g * p.ldx, l, lane);
-    if (p.W) warp_copy<cplx<R>, true>(dst + l, p.W + (long long)g * p.ldw, p.c, lane);
-  }
+  for (int s = warp; s < 2 * w; s += NW) fill_column<RPL>(slots + (long long)s * ld, p, gcol[s], lw, lane);
   __syncthreads();
 
   for (sweep = 0; sweep < p.max_sweeps; ++sweep) {
@@ -433,12 +600,12 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
           if (!xok_s) return;
         } else {
           for (int h = 0; h < 2; ++h) {
-            if (pos[h] == 0) continue;                    // block 0 never moves
+            if (pos[h] == 0) continue;
             const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
             if (!cta_wait_geq(p.flags + src, rnd, p.ctrl)) return;
-            const cplx<R>* from = p.xch + ((long long)((rnd - 1) & 1) * nb + src) * blk;
+            const float2* from = p.xch + ((long long)((rnd - 1) & 1) * nb + src) * blk;
             for (int s = warp; s < w; s += NW)
-              warp_copy<cplx<R>, true>(slots + (long long)(h * w + s) * L, from + (long long)s * L, L, lane);
+              warp_copy<float2, true>(slots + (long long)(h * w + s) * ld, from + (long long)s * ld, ld, lane);
           }
         }
         for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
@@ -448,137 +615,15 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         __syncthreads();
       }
       unsigned my_rot = 0;
-      if (r == 0) {
-        const int half = wpad / 2;
-        for (int t = 0; t < wpad - 1; ++t) {
-          for (int pi = warp; pi < 2 * half; pi += NW) {
-            const int blk = pi / half, i = pi % half;
-            int s1 = rr_player(wpad, t, i), s2 = rr_player(wpad, t, wpad - 1 - i);
-            if (s1 >= w || s2 >= w) continue;
-            s1 += blk * w; s2 += blk * w;
-            if (gcol[s1] < 0 || gcol[s2] < 0) continue;
-            my_rot += rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, l, L, p.tol, lane);
-          }
-          __syncthreads();
-        }
-      }
-      // cross phase: warp owns A columns warp*AP + a in registers
-      cplx<R> A[AP][RPL], B[AP][RPL];
-#pragma unroll
-      for (int a = 0; a < AP; ++a) {
-        const cplx<R>* src = slots + (long long)(warp * AP + a) * L;
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          const int row = lane + 32 * k;
-          A[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
-        }
-      }
-      for (int t = 0; t < w; ++t) {
-        int sb[AP];
-        bool val[AP];
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          const int ia = warp * AP + a;
-          sb[a] = w + (ia + t) % w;
-          val[a] = gcol[ia] >= 0 && gcol[sb[a]] >= 0;
-          const cplx<R>* src = slots + (long long)sb[a] * L;
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const int row = lane + 32 * k;
-            B[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
-          }
-        }
-        R da[AP], db[AP], gr[AP], gi[AP];
-        // packed two-wide FP32 (FFMA2): accumulate (x.re*y.re, x.im*y.im) style pairs
-        float2 d2a[AP], d2b[AP], g2a[AP], g2b[AP];
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          d2a[a] = make_float2(0.f, 0.f); d2b[a] = d2a[a]; g2a[a] = d2a[a]; g2b[a] = d2a[a];
-        }
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          if (lane + 32 * k < l) {
-#pragma unroll
-            for (int a = 0; a < AP; ++a) {
-              const float2 u = A[a][k], v = B[a][k];
-              d2a[a] = __ffma2_rn(u, u, d2a[a]);                         // (u.re^2, u.im^2)
-              d2b[a] = __ffma2_rn(v, v, d2b[a]);
-              g2a[a] = __ffma2_rn(u, v, g2a[a]);                         // (u.re v.re, u.im v.im)
-              g2b[a] = __ffma2_rn(u, make_float2(v.y, v.x), g2b[a]);      // (u.re v.im, u.im v.re)
-            }
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          da[a] = d2a[a].x + d2a[a].y;
-          db[a] = d2b[a].x + d2b[a].y;
-          gr[a] = g2a[a].x + g2a[a].y;          // Re(u^dagger v)
-          gi[a] = g2b[a].x - g2b[a].y;          // Im(u^dagger v)
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-          for (int a = 0; a < AP; ++a) {
-            da[a] += __shfl_xor_sync(0xffffffffu, da[a], o);
-            db[a] += __shfl_xor_sync(0xffffffffu, db[a], o);
-            gr[a] += __shfl_xor_sync(0xffffffffu, gr[a], o);
-            gi[a] += __shfl_xor_sync(0xffffffffu, gi[a], o);
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          // rotation parameters with fast reciprocal square roots: the rotation only has to be
-          // close to unitary (column norms are recomputed from theta afterwards)
-          const float g2 = gr[a] * gr[a] + gi[a] * gi[a];
-          const bool rot = val[a] && (da[a] > 0.f) && (db[a] > 0.f) && (g2 > p.tol * p.tol * da[a] * db[a]);
-          if (rot) {
-            const float rg = rsqrtf(g2);
-            const float zeta = 0.5f * (db[a] - da[a]) * rg;
-            const float z2 = 1.f + zeta * zeta;
-            const float tt = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + z2 * rsqrtf(z2));
-            const float cs = rsqrtf(1.f + tt * tt);
-            const float sn = cs * tt;
-            const float er = gr[a] * rg, ei = gi[a] * rg;
-            cplx<R>* dst = slots + (long long)sb[a] * L;
-            // x' = cs x - sn e^{-i phi} y = cs x - al y - be (y.im, -y.re)
-            // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al = sn er, be = sn ei
-            const float al = sn * er, be = sn * ei;
-            const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
-            const float2 mbe = make_float2(-be, be), pbe = make_float2(-be, be);
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              const float2 u = A[a][k], v = B[a][k];
-              float2 nu = __fmul2_rn(u, csv);
-              nu = __ffma2_rn(v, mal, nu);
-              nu = __ffma2_rn(make_float2(v.y, v.x), mbe, nu);
-              float2 nv = __fmul2_rn(v, csv);
-              nv = __ffma2_rn(u, pal, nv);
-              nv = __ffma2_rn(make_float2(u.y, u.x), pbe, nv);
-              A[a][k] = nu;
-              const int row = lane + 32 * k;
-              if (row < L) dst[row] = nv;
-            }
-            ++my_rot;
-          }
-        }
-        __syncthreads();
-      }
-#pragma unroll
-      for (int a = 0; a < AP; ++a) {
-        cplx<R>* dst = slots + (long long)(warp * AP + a) * L;
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          const int row = lane + 32 * k;
-          if (row < L) dst[row] = A[a][k];
-        }
-      }
+      if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, lane, warp, NW);
+      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, lane, warp);
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
       // shared-memory writes above must be visible to the bulk stores below
       if (bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (P > 1) {
         // publish both blocks of this round (block 0 stays in CTA 0)
-        cplx<R>* to = p.xch + (long long)(rnd & 1) * nb * blk;
+        float2* to = p.xch + (long long)(rnd & 1) * nb * blk;
         if (bulk) {
           if (threadIdx.x == 0) {
             for (int h = 0; h < 2; ++h)
@@ -592,9 +637,9 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         } else {
           for (int h = 0; h < 2; ++h) {
             if (pos[h] == 0) continue;
-            cplx<R>* base = to + (long long)pos[h] * blk;
+            float2* base = to + (long long)pos[h] * blk;
             for (int s = warp; s < w; s += NW)
-              warp_copy<cplx<R>, false>(base + (long long)s * L, slots + (long long)(h * w + s) * L, L, lane);
+              warp_copy<float2, false>(base + (long long)s * ld, slots + (long long)(h * w + s) * ld, ld, lane);
           }
           __syncthreads();
           if (threadIdx.x == 0) {
@@ -629,14 +674,9 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
     if (total == 0) { converged = true; break; }
   }
   // final blocks back to their columns
-  for (int s = warp; s < 2 * w; s += NW) {
-    const int g = gcol[s];
-    if (g < 0) continue;
-    const cplx<R>* src = slots + (long long)s * L;
-    warp_copy<cplx<R>, false>(p.X + (long long)g * p.ldx, src, l, lane);
-    if (p.W) warp_copy<cplx<R>, false>(p.W + (long long)g * p.ldw, src + l, p.c, lane);
-  }
-  if (threadIdx.x == 0) atomicAdd(&p.ctrl->jac_flops, 24.0 * (double)L * (double)rot_total);
+  for (int s = warp; s < 2 * w; s += NW) drain_column(slots + (long long)s * ld, p, gcol[s], lw, lane);
+  const double L = (double)p.l + (p.W ? (double)p.c : 0.0);
+  if (threadIdx.x == 0) atomicAdd(&p.ctrl->jac_flops, 24.0 * L * (double)rot_total);
   if (cta == 0 && threadIdx.x == 0) {
     const int used = converged ? sweep + 1 : sweep;
     p.ctrl->sweeps = used;
@@ -650,24 +690,24 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
 // one thread-block cluster (P <= 16 CTAs).  After every round each CTA reads
 // the blocks that shift into its positions straight from its neighbours'
 // shared memory (distributed shared memory) into registers, between two
-// hardware cluster barriers; no global-memory traffic, no flags.  The incoming
-// A columns are already the registers of the next cross phase.
+// hardware cluster barriers; no global-memory traffic, no flags.
 template <class R, int NW, int RPL, int AP>
 __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
+  static_assert(std::is_same<R, float>::value, "register-resident kernels are complex64");
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
+  constexpr int ld = 32 * RPL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = p.w, nb = p.nb, P = nb / 2;
-  const int L = p.l + (p.W ? p.c : 0);
-  const int l = p.l;
-  cplx<R>* slots = reinterpret_cast<cplx<R>*>(smem_raw);
-  int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * L);
+  const int lw = (p.l + 31) & ~31;
+  const int kl = p.W ? lw / 32 : RPL;
+  float2* slots = reinterpret_cast<float2*>(smem_raw);
+  int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * ld);
   __shared__ unsigned rot_s;
   __shared__ unsigned rot_slot[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cta = (int)cluster.block_rank();
   const int pos[2] = {cta, nb - 1 - cta};
-  const int wpad = w + (w & 1);
   unsigned long long rot_total = 0;
   bool converged = false;
   int sweep = 0;
@@ -690,13 +730,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
   }
   if (threadIdx.x == 0) { rot_slot[0] = 0; rot_slot[1] = 0; }
   __syncthreads();
-  for (int s = warp; s < 2 * w; s += NW) {
-    const int g = gcol[s];
-    cplx<R>* dst = slots + (long long)s * L;
-    if (g < 0) { for (int i = lane; i < L; i += 32) dst[i] = mk<R>(0, 0); continue; }
-    warp_copy<cplx<R>, true>(dst, p.X + (long long)g * p.ldx, l, lane);
-    if (p.W) warp_copy<cplx<R>, true>(dst + l, p.W + (long long)g * p.ldw, p.c, lane);
-  }
+  for (int s = warp; s < 2 * w; s += NW) fill_column<RPL>(slots + (long long)s * ld, p, gcol[s], lw, lane);
   __syncthreads();
 
   for (sweep = 0; sweep < p.max_sweeps; ++sweep) {
@@ -704,114 +738,8 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
     __syncthreads();
     for (int r = 0; r < nb - 1; ++r) {
       unsigned my_rot = 0;
-      if (r == 0) {
-        const int half = wpad / 2;
-        for (int t = 0; t < wpad - 1; ++t) {
-          for (int pi = warp; pi < 2 * half; pi += NW) {
-            const int blk = pi / half, i = pi % half;
-            int s1 = rr_player(wpad, t, i), s2 = rr_player(wpad, t, wpad - 1 - i);
-            if (s1 >= w || s2 >= w) continue;
-            s1 += blk * w; s2 += blk * w;
-            if (gcol[s1] < 0 || gcol[s2] < 0) continue;
-            my_rot += rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, l, L, p.tol, lane);
-          }
-          __syncthreads();
-        }
-      }
-      cplx<R> A[AP][RPL], B[AP][RPL];
-#pragma unroll
-      for (int a = 0; a < AP; ++a) {
-        const cplx<R>* src = slots + (long long)(warp * AP + a) * L;
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          const int row = lane + 32 * k;
-          A[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
-        }
-      }
-      for (int t = 0; t < w; ++t) {
-        int sb[AP];
-        bool val[AP];
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          const int ia = warp * AP + a;
-          sb[a] = w + (ia + t) % w;
-          val[a] = gcol[ia] >= 0 && gcol[sb[a]] >= 0;
-          const cplx<R>* src = slots + (long long)sb[a] * L;
-#pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const int row = lane + 32 * k;
-            B[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
-          }
-        }
-        float2 d2a[AP], d2b[AP], g2a[AP], g2b[AP];
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          d2a[a] = make_float2(0.f, 0.f); d2b[a] = d2a[a]; g2a[a] = d2a[a]; g2b[a] = d2a[a];
-        }
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          if (lane + 32 * k < l) {
-#pragma unroll
-            for (int a = 0; a < AP; ++a) {
-              const float2 u = A[a][k], v = B[a][k];
-              d2a[a] = __ffma2_rn(u, u, d2a[a]);
-              d2b[a] = __ffma2_rn(v, v, d2b[a]);
-              g2a[a] = __ffma2_rn(u, v, g2a[a]);
-              g2b[a] = __ffma2_rn(u, make_float2(v.y, v.x), g2b[a]);
-            }
-          }
-        }
-        float da[AP], db[AP], gr[AP], gi[AP];
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          da[a] = d2a[a].x + d2a[a].y; db[a] = d2b[a].x + d2b[a].y;
-          gr[a] = g2a[a].x + g2a[a].y; gi[a] = g2b[a].x - g2b[a].y;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-          for (int a = 0; a < AP; ++a) {
-            da[a] += __shfl_xor_sync(0xffffffffu, da[a], o);
-            db[a] += __shfl_xor_sync(0xffffffffu, db[a], o);
-            gr[a] += __shfl_xor_sync(0xffffffffu, gr[a], o);
-            gi[a] += __shfl_xor_sync(0xffffffffu, gi[a], o);
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < AP; ++a) {
-          float cs, sn, er, ei;
-          if (val[a] && rot_params<float>(da[a], db[a], gr[a], gi[a], p.tol, cs, sn, er, ei)) {
-            cplx<R>* dst = slots + (long long)sb[a] * L;
-            const float al = sn * er, be = sn * ei;
-            const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
-            const float2 pbe = make_float2(-be, be);
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              const float2 u = A[a][k], v = B[a][k];
-              float2 nu = __fmul2_rn(u, csv);
-              nu = __ffma2_rn(v, mal, nu);
-              nu = __ffma2_rn(make_float2(v.y, v.x), pbe, nu);
-              float2 nv = __fmul2_rn(v, csv);
-              nv = __ffma2_rn(u, pal, nv);
-              nv = __ffma2_rn(make_float2(u.y, u.x), pbe, nv);
-              A[a][k] = nu;
-              const int row = lane + 32 * k;
-              if (row < L) dst[row] = nv;
-            }
-            ++my_rot;
-          }
-        }
-        __syncthreads();
-      }
-#pragma unroll
-      for (int a = 0; a < AP; ++a) {
-        cplx<R>* dst = slots + (long long)(warp * AP + a) * L;
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) {
-          const int row = lane + 32 * k;
-          if (row < L) dst[row] = A[a][k];
-        }
-      }
+      if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, lane, warp, NW);
+      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, lane, warp);
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
       __syncthreads();
       const bool last = (r == nb - 2);
@@ -822,19 +750,16 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
         // block for their A half (position i+1), CTA 0 takes position 1's block for its B half
         // and keeps it in registers to the end (its own B half is still read in phase 2).
         // Phase 2: CTAs 1..P-1 take the block for their B half (position nb-i).
-        cplx<R> in[AP][RPL];
+        float2 in[AP][RPL];
         {
           const int rk = (cta == 0) ? srank[1] : srank[0];
           const int hf = (cta == 0) ? shalf[1] : shalf[0];
-          const cplx<R>* remote = cluster.map_shared_rank(slots, rk);
+          const float2* remote = cluster.map_shared_rank(slots, rk);
 #pragma unroll
           for (int a = 0; a < AP; ++a) {
-            const cplx<R>* src = remote + (long long)(hf * w + warp * AP + a) * L;
+            const float2* src = remote + (long long)(hf * w + warp * AP + a) * ld + lane;
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              const int row = lane + 32 * k;
-              in[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
-            }
+            for (int k = 0; k < RPL; ++k) in[a][k] = src[32 * k];
           }
         }
         unsigned vote = 0;
@@ -845,33 +770,24 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
         if (cta != 0) {
 #pragma unroll
           for (int a = 0; a < AP; ++a) {
-            cplx<R>* dst = slots + (long long)(warp * AP + a) * L;
+            float2* dst = slots + (long long)(warp * AP + a) * ld + lane;
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              const int row = lane + 32 * k;
-              if (row < L) dst[row] = in[a][k];
-            }
+            for (int k = 0; k < RPL; ++k) dst[32 * k] = in[a][k];
           }
-          const cplx<R>* remote = cluster.map_shared_rank(slots, srank[1]);
+          const float2* remote = cluster.map_shared_rank(slots, srank[1]);
 #pragma unroll
           for (int a = 0; a < AP; ++a) {
-            const cplx<R>* src = remote + (long long)(shalf[1] * w + warp * AP + a) * L;
+            const float2* src = remote + (long long)(shalf[1] * w + warp * AP + a) * ld + lane;
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-              const int row = lane + 32 * k;
-              in[a][k] = (row < L) ? src[row] : mk<R>(0, 0);
-            }
+            for (int k = 0; k < RPL; ++k) in[a][k] = src[32 * k];
           }
         }
         cluster.sync();   // phase-2 sources read
 #pragma unroll
         for (int a = 0; a < AP; ++a) {
-          cplx<R>* dst = slots + (long long)(w + warp * AP + a) * L;
+          float2* dst = slots + (long long)(w + warp * AP + a) * ld + lane;
 #pragma unroll
-          for (int k = 0; k < RPL; ++k) {
-            const int row = lane + 32 * k;
-            if (row < L) dst[row] = in[a][k];
-          }
+          for (int k = 0; k < RPL; ++k) dst[32 * k] = in[a][k];
         }
         const int rn = last ? 0 : r + 1;
         for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
@@ -888,14 +804,9 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
     if (total == 0) { converged = true; break; }
   }
   // final blocks back to their columns
-  for (int s = warp; s < 2 * w; s += NW) {
-    const int g = gcol[s];
-    if (g < 0) continue;
-    const cplx<R>* src = slots + (long long)s * L;
-    warp_copy<cplx<R>, false>(p.X + (long long)g * p.ldx, src, l, lane);
-    if (p.W) warp_copy<cplx<R>, false>(p.W + (long long)g * p.ldw, src + l, p.c, lane);
-  }
-  if (threadIdx.x == 0) atomicAdd(&p.ctrl->jac_flops, 24.0 * (double)L * (double)rot_total);
+  for (int s = warp; s < 2 * w; s += NW) drain_column(slots + (long long)s * ld, p, gcol[s], lw, lane);
+  const double L = (double)p.l + (p.W ? (double)p.c : 0.0);
+  if (threadIdx.x == 0) atomicAdd(&p.ctrl->jac_flops, 24.0 * L * (double)rot_total);
   if (cta == 0 && threadIdx.x == 0) {
     const int used = converged ? sweep + 1 : sweep;
     p.ctrl->sweeps = used;
@@ -911,16 +822,19 @@ struct Variant { int nw, rpl, ap; const void* fn; };
 
 #define EAMPS_V(NW, RPL, AP) {NW, RPL, AP, (const void*)jacobi_kernel3<float, NW, RPL, AP>}
 const Variant kVariants[] = {
-    EAMPS_V(4, 4, 1),  EAMPS_V(8, 4, 1),  EAMPS_V(16, 4, 1), EAMPS_V(8, 4, 2),  EAMPS_V(16, 4, 2),
-    EAMPS_V(4, 8, 1),  EAMPS_V(8, 8, 1),  EAMPS_V(16, 8, 1), EAMPS_V(4, 8, 2),  EAMPS_V(8, 8, 2), EAMPS_V(16, 8, 2),
+    EAMPS_V(4, 4, 1),  EAMPS_V(8, 4, 1),  EAMPS_V(16, 4, 1),  EAMPS_V(8, 4, 2),  EAMPS_V(16, 4, 2),
+    EAMPS_V(4, 8, 1),  EAMPS_V(8, 8, 1),  EAMPS_V(16, 8, 1),  EAMPS_V(4, 8, 2),  EAMPS_V(8, 8, 2), EAMPS_V(16, 8, 2),
+    EAMPS_V(4, 12, 1), EAMPS_V(8, 12, 1), EAMPS_V(4, 12, 2),  EAMPS_V(8, 12, 2),
     EAMPS_V(4, 16, 1), EAMPS_V(8, 16, 1), EAMPS_V(16, 16, 1), EAMPS_V(4, 16, 2), EAMPS_V(8, 16, 2),
+    EAMPS_V(4, 24, 1), EAMPS_V(8, 24, 1),
     EAMPS_V(4, 32, 1), EAMPS_V(8, 32, 1),
 };
 #undef EAMPS_V
 
 #define EAMPS_C(NW, RPL) {NW, RPL, 1, (const void*)jacobi_cluster_kernel<float, NW, RPL, 1>}
 const Variant kClusterVariants[] = {
-    EAMPS_C(8, 4), EAMPS_C(16, 4), EAMPS_C(8, 8), EAMPS_C(16, 8), EAMPS_C(8, 16), EAMPS_C(16, 16),
+    EAMPS_C(8, 4),  EAMPS_C(16, 4), EAMPS_C(8, 8),  EAMPS_C(16, 8), EAMPS_C(8, 12),
+    EAMPS_C(8, 16), EAMPS_C(16, 16), EAMPS_C(8, 24), EAMPS_C(8, 32),
 };
 #undef EAMPS_C
 
@@ -945,8 +859,9 @@ int env_int(const char* name, int dflt) {
   return (v && *v) ? std::atoi(v) : dflt;
 }
 
+// Rows per lane of the register-resident kernels for padded columns of L rows (0: too long).
 int rows_per_lane(int L) {
-  for (int r : {4, 8, 16, 32})
+  for (int r : {4, 8, 12, 16, 24, 32})
     if (32 * r >= L) return r;
   return 0;
 }
@@ -976,8 +891,10 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
   JacobiPlan plan;
   const int L = l + (accumulate ? c : 0);
   const size_t budget = 200 * 1024;
-  const size_t col_bytes = (size_t)L * sizeof(cplx<R>);
-  const int rpl = rows_per_lane(L);
+  // register-resident kernels: padded columns (W rows start at l rounded up to 32)
+  const int Lreg = accumulate ? ((l + 31) & ~31) + c : l;
+  const int rpl = rows_per_lane(Lreg);
+  const size_t col_bytes = (size_t)32 * rpl * sizeof(cplx<R>);
   if (std::is_same<R, float>::value && rpl > 0 && rpl <= 16 && env_int("EAMPS_JACOBI_CLUSTER", 1)) {
     // whole matrix in one cluster of at most 16 CTAs with 8 warps each (w = 8), i.e. up to 256
     // columns; wider blocks (16 warps) were measured slower than the point-to-point kernel on
@@ -995,6 +912,7 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
         plan.fn = v->fn;
         plan.threads = v->nw * 32;
         plan.cluster = P;
+        plan.ld = 32 * rpl;
         return plan;
       }
     }
@@ -1042,11 +960,13 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
       plan.smem = smem;
       plan.fn = v->fn;
       plan.threads = v->nw * 32;
+      plan.ld = 32 * rpl;
       return plan;
     }
   }
   // shared-memory kernel
-  int w_fit = (int)std::max<size_t>(1, budget / (2 * col_bytes + 8));
+  const size_t col_bytes_v1 = (size_t)L * sizeof(cplx<R>);
+  int w_fit = (int)std::max<size_t>(1, budget / (2 * col_bytes_v1 + 8));
   int half = (c + 1) / 2;
   if (half <= w_fit && c <= 128) {
     plan.w = std::max(1, half);
@@ -1064,6 +984,7 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
     plan.nb = 2 * P;
   }
   plan.smem = (size_t)2 * plan.w * L * sizeof(cplx<R>) + 2 * plan.w * sizeof(int) + 16;
+  plan.ld = L;
   plan.fn = (const void*)jacobi_kernel<R>;
   plan.threads = 256;
   return plan;
@@ -1074,8 +995,7 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
                           cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cplx<R>* xch,
                           size_t xch_cap, unsigned* flags, int flags_cap, cudaStream_t st) {
   if (c <= 1) return cudaSuccess;   // a single column is already orthogonal
-  const size_t L = (size_t)l + (W ? c : 0);
-  if ((size_t)2 * plan.nb * plan.w * L > xch_cap || plan.nb > flags_cap) return cudaErrorInvalidValue;
+  if ((size_t)2 * plan.nb * plan.w * (size_t)plan.ld > xch_cap || plan.nb > flags_cap) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(plan.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
   if (e != cudaSuccess) return e;
   // reset barrier and sweep counters (bar_count, bar_gen, rot[3] are contiguous) and the position flags

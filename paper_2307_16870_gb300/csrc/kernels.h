@@ -20,10 +20,11 @@ struct JacobiPlan {
   const void* fn = nullptr;  // kernel variant
   int threads = 256;
   int cluster = 0;           // > 0: cluster-resident kernel, one cluster of this many CTAs
+  int ld = 0;                // column stride (complex entries) in shared memory and the exchange slots
 };
 template <class R>
 JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas);
-// xch: exchange slots of the multi-CTA kernels (2 * nb * w * (l + c if W) complex entries at
+// xch: exchange slots of the multi-CTA kernels (2 * nb * w * plan.ld complex entries at
 // most xch_cap); flags: nb position flags (at most flags_cap).
 template <class R>
 cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int l, int c,
