@@ -59,6 +59,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    ap.add_argument("--study", default="", choices=["", "ttf", "mpo"],
+                    help="ttf: time to target fidelity, EA against fixed bond dimensions; "
+                         "mpo: the noisy EA-MPO workload (d = 4)")
     ap.add_argument("--micro", type=int, default=0, metavar="CHI",
                     help="instead of the circuit: a few two-site updates on a random canonical 24-site MPS "
                          "with every bond CHI (the launch configuration of the circuit's saturated gates)")
@@ -324,6 +327,94 @@ def run_ours(a) -> int:
     return 0
 
 
+def _timed_circuit(E, torch, dev, n_qubits, qs, ops_dev, op_dim, **mps_kw):
+    """One run of a whole circuit from |0...0> (a pure state, or |0...0><0...0| for kind MIXED);
+    returns (GPU ms, inferred fidelity, max bond, Jacobi ms, Jacobi launches)."""
+    stream = torch.cuda.current_stream(dev)
+    m = E.MPS(n_qubits, log_truncations=False, stream=stream.cuda_stream, **mps_kw)
+    m.profile(True)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    E.mps_apply_circuit_device(m.h, qs, ops_dev.data_ptr(), op_dim)
+    fid = m.fidelity()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    st = m.stats()
+    out = (e0.elapsed_time(e1), fid, max(m.bond_dims()), st["jacobi_ms"], st["jacobi_launches"])
+    m.close()
+    return out
+
+
+def run_study(a) -> int:
+    """Measurement studies on one GPU, one JSON line per run and a summary line.
+
+    ttf: the paper's time-to-fidelity methodology (EA run at F_min records its
+    largest bond; fixed-bond runs at that bond and at 128/256/512), on 100-qubit
+    Haar brickworks of depth 8 (EA reaches F_min below the cap) and depth 30
+    (every run is cap-bound).  mpo: the noisy 30-qubit depth-15 brickwork as a
+    density matrix (d = 4): every gate fused with two-qubit depolarising noise
+    p = 0.01 and amplitude damping gamma = 0.005 on both qubits, F_min = 0.95.
+    """
+    import torch
+    import paper_2307_16870_gb300 as E
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prec = {"tf32x3": E.TF32X3, "fp32": E.FP32, "fp64": E.FP64}[a.precision]
+    rows = []
+
+    def emit(row):
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+
+    if a.study == "ttf":
+        for depth in (8, 30):
+            circ = W.brickwork_circuit(100, depth, a.seed)
+            n = circ.n_2q
+            ops_dev = torch.from_numpy(circ.ops_array().view(np.float64).reshape(n, 32).copy()).to(dev)
+            qs = np.asarray(circ.qs, dtype=np.int32)
+            # warm-up (kernel loading, allocation)
+            _timed_circuit(E, torch, dev, 100, qs[:50], ops_dev, 4, f_min=0.9, n_2q=n, chi_max=64, precision=prec)
+            for f_min in (0.9, 0.5):
+                for cap in (256, 512):
+                    ms, fid, mx, jms, jl = _timed_circuit(E, torch, dev, 100, qs, ops_dev, 4, f_min=f_min, n_2q=n,
+                                                          strategy=E.GLOBAL, chi_max=cap, precision=prec)
+                    emit({"study": "ttf", "depth": depth, "n_2q": n, "mode": "EA", "f_min": f_min, "chi_cap": cap,
+                          "gpu_s": ms / 1e3, "updates_per_s": n / (ms / 1e3), "inferred_fidelity": fid,
+                          "max_bond": mx, "reached_f_min": bool(fid >= f_min), "jacobi_share": jms / ms})
+            chis = sorted({128, 256, 512} | {r["max_bond"] for r in rows if r.get("depth") == depth})
+            for chi in chis:
+                ms, fid, mx, jms, jl = _timed_circuit(E, torch, dev, 100, qs, ops_dev, 4, n_2q=n, fixed_chi=chi,
+                                                      chi_max=chi, precision=prec)
+                emit({"study": "ttf", "depth": depth, "n_2q": n, "mode": "fixed", "chi": chi, "gpu_s": ms / 1e3,
+                      "updates_per_s": n / (ms / 1e3), "inferred_fidelity": fid, "max_bond": mx,
+                      "jacobi_share": jms / ms})
+    elif a.study == "mpo":
+        n_q, depth, p, gamma = 30, 15, 0.01, 0.005
+        circ = W.brickwork_circuit(n_q, depth, a.seed)
+        n = circ.n_2q
+        ad = E.mps_superop_from_kraus(W.amplitude_damping_kraus(gamma), 1)
+        dep = E.mps_superop_from_kraus(W.depolarizing_2q_kraus(p), 2)
+        ops = np.stack([np.kron(ad, ad) @ dep @ E.mps_superop_from_kraus([u], 2) for u in circ.ops])
+        ops_dev = torch.from_numpy(np.ascontiguousarray(ops).view(np.float64).reshape(n, 512).copy()).to(dev)
+        qs = np.asarray(circ.qs, dtype=np.int32)
+        _timed_circuit(E, torch, dev, n_q, qs[:20], ops_dev, 16, kind=E.MIXED, f_min=0.95, n_2q=n, chi_max=64,
+                       precision=prec)
+        for mixed_fid in (E.KEPT_RATIO, E.WANG_SQRT):
+            for cap in (128, 256):
+                ms, fid, mx, jms, jl = _timed_circuit(E, torch, dev, n_q, qs, ops_dev, 16, kind=E.MIXED, f_min=0.95,
+                                                      n_2q=n, strategy=E.GLOBAL, chi_max=cap, precision=prec,
+                                                      mixed_fid=mixed_fid)
+                emit({"study": "mpo", "n_qubits": n_q, "depth": depth, "n_2q": n, "p_depol": p, "gamma_ad": gamma,
+                      "f_min": 0.95, "mixed_fid": "kept_ratio" if mixed_fid == E.KEPT_RATIO else "wang_sqrt",
+                      "chi_cap": cap, "gpu_s": ms / 1e3, "updates_per_s": n / (ms / 1e3),
+                      "inferred_fidelity": fid, "max_bond": mx, "jacobi_share": jms / ms})
+    print(json.dumps({"study": a.study, "runs": len(rows), "precision": a.precision,
+                      "device": torch.cuda.get_device_name(dev)}), flush=True)
+    return 0
+
+
 def run_micro(a) -> int:
     """Per-launch Jacobi timing of saturated updates (used for focused profiling)."""
     import torch
@@ -351,6 +442,8 @@ def main(argv=None) -> int:
     a = parse_args(argv)
     if a.micro:
         return run_micro(a)
+    if a.study:
+        return run_study(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)
