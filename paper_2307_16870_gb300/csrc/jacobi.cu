@@ -74,6 +74,28 @@ __device__ __forceinline__ bool rot_params<float>(float a, float b, float gr, fl
   return true;
 }
 
+// FP32 rotation of the register-resident kernels in the form the column update uses:
+// cs = cos, (al, be) = sin * e^{i phi} split into real and imaginary parts.  With
+// u = b - a, v = 2|g| and D = |u| + sqrt(u^2 + v^2): tan = sign(u) v / D, so
+// cs = D / sqrt(D^2 + v^2) and sin e^{i phi} = sign(u) 2 g / sqrt(D^2 + v^2) -- the same
+// angle as rot_params<float>, with two reciprocal square roots instead of four
+// dependent special-function operations.  cs^2 + |sin|^2 = 1 to rsqrt accuracy.
+__device__ __forceinline__ bool rot_params_fused(float a, float b, float gr, float gi, float tol, float& cs, float& al,
+                                                 float& be) {
+  const float g2 = gr * gr + gi * gi;
+  if (!(a > 0.f) || !(b > 0.f) || !(g2 > tol * tol * a * b)) return false;
+  const float u = b - a;
+  const float x = fmaf(u, u, 4.f * g2);
+  const float h = x * rsqrtf(x);
+  const float D = fabsf(u) + h;
+  const float r = rsqrtf(fmaf(D, D, 4.f * g2));
+  const float s2 = (u >= 0.f) ? 2.f * r : -2.f * r;
+  cs = D * r;
+  al = s2 * gr;
+  be = s2 * gi;
+  return true;
+}
+
 // Orthogonalise columns x and y (length L, of which the first l enter the
 // inner products).  Returns 1 if a rotation was applied.
 template <class R>
@@ -193,9 +215,15 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void bulk_store_drain() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until at most N committed bulk groups of this thread are pending (older ones complete).
+template <int N>
+__device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory"); }
+// Make completed bulk stores visible at GPU scope, then release a flag.
+__device__ __forceinline__ void publish_flag(unsigned* flag, unsigned v) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __threadfence();
+  st_release(flag, v);
 }
 
 template <class R>
@@ -465,11 +493,10 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
     warp_allreduce<4 * AP>(s, lane);
 #pragma unroll
     for (int a = 0; a < AP; ++a) {
-      float cs, sn, er, ei;
-      if (rot_params<float>(s[4 * a], s[4 * a + 1], s[4 * a + 2], s[4 * a + 3], tol, cs, sn, er, ei)) {
+      float cs, al, be;
+      if (rot_params_fused(s[4 * a], s[4 * a + 1], s[4 * a + 2], s[4 * a + 3], tol, cs, al, be)) {
         // x' = cs x - sn e^{-i phi} y = cs x - al y - be (y.im, -y.re)
-        // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al = sn er, be = sn ei
-        const float al = sn * er, be = sn * ei;
+        // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al + i be = sn e^{i phi}
         const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
         const float2 pbe = make_float2(-be, be);
 #pragma unroll
@@ -626,13 +653,14 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         float2* to = p.xch + (long long)(rnd & 1) * nb * blk;
         if (bulk) {
           if (threadIdx.x == 0) {
-            for (int h = 0; h < 2; ++h)
-              if (pos[h] != 0) bulk_store(to + (long long)pos[h] * blk, slots + h * blk, blk_bytes);
-            bulk_store_drain();   // also ends the reads of shared memory before the next loads
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-            __threadfence();
-            if (pos[0] != 0) st_release(p.flags + pos[0], rnd + 1);
-            st_release(p.flags + pos[1], rnd + 1);
+            // one bulk group per block, each flag released as soon as its own block has landed;
+            // the final wait also ends the reads of shared memory before the next loads
+            if (pos[0] != 0) { bulk_store(to + (long long)pos[0] * blk, slots, blk_bytes); bulk_commit(); }
+            bulk_store(to + (long long)pos[1] * blk, slots + blk, blk_bytes);
+            bulk_commit();
+            if (pos[0] != 0) { bulk_wait<1>(); publish_flag(p.flags + pos[0], rnd + 1); }
+            bulk_wait<0>();
+            publish_flag(p.flags + pos[1], rnd + 1);
           }
         } else {
           for (int h = 0; h < 2; ++h) {
