@@ -59,9 +59,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
-    ap.add_argument("--study", default="", choices=["", "ttf", "mpo"],
+    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch"],
                     help="ttf: time to target fidelity, EA against fixed bond dimensions; "
-                         "mpo: the noisy EA-MPO workload (d = 4)")
+                         "mpo: the noisy EA-MPO workload (d = 4); "
+                         "batch: 64 independent circuits run concurrently")
     ap.add_argument("--micro", type=int, default=0, metavar="CHI",
                     help="instead of the circuit: a few two-site updates on a random canonical 24-site MPS "
                          "with every bond CHI (the launch configuration of the circuit's saturated gates)")
@@ -356,6 +357,9 @@ def run_study(a) -> int:
     (every run is cap-bound).  mpo: the noisy 30-qubit depth-15 brickwork as a
     density matrix (d = 4): every gate fused with two-qubit depolarising noise
     p = 0.01 and amplitude damping gamma = 0.005 on both qubits, F_min = 0.95.
+    batch: 64 independent brickworks (N ~ U[20, 80], depth ~ U[10, 30], F_min in
+    {0.9, 0.99}, bond cap 128) through mps_batch_run at concurrency 1, 4, 8, 16;
+    wall time of the whole batch (host threads included).
     """
     import torch
     import paper_2307_16870_gb300 as E
@@ -410,6 +414,34 @@ def run_study(a) -> int:
                       "f_min": 0.95, "mixed_fid": "kept_ratio" if mixed_fid == E.KEPT_RATIO else "wang_sqrt",
                       "chi_cap": cap, "gpu_s": ms / 1e3, "updates_per_s": n / (ms / 1e3),
                       "inferred_fidelity": fid, "max_bond": mx, "jacobi_share": jms / ms})
+    elif a.study == "batch":
+        specs = W.random_batch_specs(64, a.seed)
+        cap = 128
+        circs, devs = [], []
+        for sp in specs:
+            c = W.brickwork_circuit(sp["n_qubits"], sp["depth"], sp["seed"])
+            circs.append(c)
+            devs.append(torch.from_numpy(c.ops_array().view(np.float64).reshape(c.n_2q, 32).copy()).to(dev))
+        total = sum(c.n_2q for c in circs)
+        items = [{"n_qubits": sp["n_qubits"], "qs": c.qs, "ops_dev": dv.data_ptr(), "op_dim": 4,
+                  "f_min": sp["f_min"], "n_2q": c.n_2q, "chi_max": cap, "precision": prec}
+                 for sp, c, dv in zip(specs, circs, devs)]
+        E.mps_batch_run(items[:4], concurrency=4)          # warm-up (kernel loading)
+        base = None
+        for conc in (1, 4, 8, 16):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            code, res = E.mps_batch_run(items, concurrency=conc)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            fids = [r["fidelity"] for r in res]
+            if base is None:
+                base = fids
+            emit({"study": "batch", "circuits": len(items), "gates": total, "chi_cap": cap, "concurrency": conc,
+                  "wall_s": dt, "updates_per_s": total / dt, "status": code,
+                  "same_fidelities_as_sequential": fids == base,
+                  "reached_f_min": sum(1 for r, sp in zip(res, specs) if r["fidelity"] >= sp["f_min"]),
+                  "max_bond": max(r["max_bond"] for r in res)})
     print(json.dumps({"study": a.study, "runs": len(rows), "precision": a.precision,
                       "device": torch.cuda.get_device_name(dev)}), flush=True)
     return 0

@@ -144,6 +144,39 @@ mps_status mps_apply_2q_device(mps_handle h, int q, const double* op_dev, int op
 mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev,
                                     int op_dim, double target);
 
+/* One circuit of a batch (mps_batch_run).  The inputs are read and the
+ * outputs written by the call; the item array is owned by the caller. */
+typedef struct {
+  int n_qubits;            /* chain length, >= 2 */
+  int n_gates;             /* two-qubit gates in the circuit */
+  const int* qs;           /* HOST, n_gates entries: gate g acts on (qs[g], qs[g]+1) */
+  const double* ops_dev;   /* DEVICE, n_gates operators of 2*op_dim*op_dim doubles (row-major complex) */
+  int op_dim;              /* 4 (PURE: unitary) or 16 (MIXED: superoperator) */
+  double target;           /* as for mps_apply_2q: < 0 schedule, >= 1 no truncation, else per-truncation */
+  mps_options opt;         /* options of this circuit's handle */
+  double fidelity;         /* out: running product of truncation fidelities (Eq. prod) */
+  int max_bond;            /* out: largest bond dimension after the circuit */
+  int status;              /* out: mps_status of this circuit */
+} mps_batch_item;
+
+/* Run many independent circuits, each one the gate-by-gate algorithm of
+ * the "Entanglement-aware" section (as mps_apply_circuit_device from
+ * |0...0>), up to `concurrency` at a time: every circuit has its own handle
+ * and CUDA stream, driven by its own host thread; the longest circuits
+ * (gates x qubits) start first.  With concurrency > 1 the multi-CTA Jacobi
+ * launches of all running circuits share one budget of co-resident CTAs per
+ * device, so no grid waits on CTAs that cannot become resident.  Each
+ * circuit's results are those of running it alone.
+ * keep: NULL (each handle is destroyed when its circuit ends) or an array of
+ * `count` handles that receives every circuit's handle (it owns its stream;
+ * release with mps_destroy).  The device operators must stay valid until
+ * the call returns.
+ * Returns MPS_OK; MPS_WARN_CHI_CAP when some circuit reached its bond cap;
+ * else the error of the first failing item (each item's status is in
+ * items[i].status).  MPS_ERR_ARG: count < 0, items == NULL with count > 0,
+ * or concurrency < 1. */
+mps_status mps_batch_run(mps_batch_item* items, int count, int concurrency, mps_handle* keep);
+
 /* *inferred = running product of truncation fidelities (Eq. prod), FP64. */
 mps_status mps_fidelity(mps_handle h, double* inferred);
 

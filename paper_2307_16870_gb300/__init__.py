@@ -26,7 +26,7 @@ __all__ = [
     "mps_bond_dims", "mps_centre", "mps_get_site", "mps_lognorm", "mps_last_singular_values",
     "mps_truncation_log", "mps_sync", "mps_superop_from_kraus", "mps_status_string",
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
-    "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc",
+    "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run",
 ]
 
 PURE, MIXED = 0, 1
@@ -44,6 +44,13 @@ class MpsOptions(C.Structure):
     _fields_ = [("kind", C.c_int), ("f_min", C.c_double), ("n_2q", C.c_longlong), ("strategy", C.c_int),
                 ("chi_max", C.c_int), ("fixed_chi", C.c_int), ("precision", C.c_int), ("mixed_fid", C.c_int),
                 ("max_sweeps", C.c_int), ("log_truncations", C.c_int)]
+
+
+class BatchItem(C.Structure):
+    """One circuit of mps_batch_run (same layout as the C struct)."""
+    _fields_ = [("n_qubits", C.c_int), ("n_gates", C.c_int), ("qs", C.POINTER(C.c_int)), ("ops_dev", C.c_void_p),
+                ("op_dim", C.c_int), ("target", C.c_double), ("opt", MpsOptions), ("fidelity", C.c_double),
+                ("max_bond", C.c_int), ("status", C.c_int)]
 
 
 class TruncRecord(C.Structure):
@@ -110,6 +117,7 @@ def load(path: str | None = None):
         "mps_profile": (C.c_int, [H, C.c_int]),
         "mps_stats": (C.c_int, [H, C.POINTER(MpsStats)]),
         "mps_stats_reset": (C.c_int, [H]),
+        "mps_batch_run": (C.c_int, [C.POINTER(BatchItem), C.c_int, C.c_int, C.POINTER(H)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -297,6 +305,45 @@ def mps_cgemm_c64_noalloc(M: int, N: int, K: int, alpha: float, A: int, a_rs: in
                                                C.c_void_p(stream or None)), "mps_cgemm_c64_noalloc")
 
 
+def mps_batch_run(circuits: list, concurrency: int = 4, keep: bool = False):
+    """Run independent circuits concurrently (see mps_batch_run in include/eamps.h).
+
+    circuits: dicts with n_qubits, qs (gate left qubits), ops_dev (device pointer to the
+    gates, 2*op_dim*op_dim doubles each), op_dim, and optionally target and the MPS option
+    names (kind, f_min, n_2q, strategy, chi_max, fixed_chi, precision, mixed_fid, max_sweeps).
+    Returns (status, results) with one dict per circuit (fidelity, max_bond, status and, with
+    keep, an MPS object adopting the circuit's handle)."""
+    n = len(circuits)
+    items = (BatchItem * max(n, 1))()
+    qs_keep = []
+    for i, c in enumerate(circuits):
+        q = np.ascontiguousarray(np.asarray(c["qs"], dtype=np.int32))
+        qs_keep.append(q)
+        it = items[i]
+        it.n_qubits, it.n_gates = int(c["n_qubits"]), int(q.size)
+        it.qs = q.ctypes.data_as(C.POINTER(C.c_int))
+        it.ops_dev = C.c_void_p(int(c["ops_dev"]))
+        it.op_dim = int(c.get("op_dim", 4))
+        it.target = float(c.get("target", -1.0))
+        o = mps_default_options()
+        for name in ("kind", "f_min", "n_2q", "strategy", "chi_max", "fixed_chi", "precision", "mixed_fid",
+                     "max_sweeps"):
+            if name in c:
+                setattr(o, name, c[name])
+        o.log_truncations = int(c.get("log_truncations", 0))
+        it.opt = o
+    handles = (C.c_void_p * max(n, 1))() if keep else None
+    code = load().mps_batch_run(items, n, int(concurrency), handles)
+    results = []
+    for i, c in enumerate(circuits):
+        r = {"fidelity": items[i].fidelity, "max_bond": items[i].max_bond, "status": items[i].status}
+        if keep and handles[i]:
+            r["mps"] = MPS.adopt(handles[i], int(c["n_qubits"]), int(c.get("kind", PURE)))
+        results.append(r)
+    del qs_keep
+    return code, results
+
+
 def mps_superop_from_kraus(kraus: list, nq: int) -> np.ndarray:
     ks = np.concatenate([_cplx(k) for k in kraus])
     out = np.zeros(2 * 16 ** nq)
@@ -321,6 +368,13 @@ class MPS:
         self.kind = kind
         self.d = 2 if kind == PURE else 4
         self.h = mps_create(n_qubits, o, stream)
+
+    @classmethod
+    def adopt(cls, handle: int, n_qubits: int, kind: int = PURE) -> "MPS":
+        """Wrap an existing handle (e.g. one kept by mps_batch_run); the object destroys it."""
+        obj = cls.__new__(cls)
+        obj.n, obj.kind, obj.d, obj.h = n_qubits, kind, 2 if kind == PURE else 4, handle
+        return obj
 
     def close(self):
         if getattr(self, "h", None):

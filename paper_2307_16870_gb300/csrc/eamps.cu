@@ -3,12 +3,17 @@
 // device kernels of this directory; the host plans launches, tracks the bond
 // sizes it reads back after each truncation, and marshals arguments.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstddef>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <numeric>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -21,6 +26,36 @@ using namespace eamps;
 namespace {
 
 constexpr int kDefaultCap = 1024;
+
+// Co-resident CTAs of multi-CTA Jacobi launches (cooperative grids whose CTAs wait on one
+// another, and clusters) on one device, shared by every handle that runs in a batch.  A
+// handle holds CTAs from before such a launch until its next stream synchronisation; a
+// handle that needs more than it holds first synchronises and returns what it holds, so a
+// waiting handle never holds any and concurrent grids never exceed the device.
+struct CoopBudget {
+  std::mutex m;
+  std::condition_variable cv;
+  int free_ctas = -1;
+  void acquire(int n, int capacity) {
+    std::unique_lock<std::mutex> lk(m);
+    if (free_ctas < 0) free_ctas = capacity;
+    n = std::min(n, capacity);
+    cv.wait(lk, [&] { return free_ctas >= n; });
+    free_ctas -= n;
+  }
+  void release(int n) {
+    {
+      std::lock_guard<std::mutex> lk(m);
+      free_ctas += n;
+    }
+    cv.notify_all();
+  }
+};
+
+CoopBudget& coop_budget(int device) {
+  static CoopBudget budgets[64];
+  return budgets[device & 63];
+}
 
 mps_status from_bits(int bits) {
   if (bits & ST_TIMEOUT) return MPS_ERR_TIMEOUT;
@@ -83,6 +118,10 @@ struct mps_state {
   bool log_on = true;
   int sticky = 0;
   cudaStream_t stream = nullptr;
+  bool owns_stream = false;   // stream created for this handle (batch runs); destroyed with it
+  bool shared_gpu = false;    // runs beside other handles: multi-CTA launches go through the budget
+  int device = 0;
+  int coop_held = 0;          // CTAs held in the device budget
 };
 
 namespace {
@@ -125,6 +164,7 @@ struct Engine final : mps_state {
 
   ~Engine() override {
     if (stream) cudaStreamSynchronize(stream);
+    coop_release();
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
                     ctrl, wdev, w2dev, work, outdev, stage, xch, jflags};
     for (void* b : bufs) if (b) cudaFree(b);
@@ -133,6 +173,24 @@ struct Engine final : mps_state {
     if (tc) tc_destroy(tc);
     for (auto& t : pending) { ev_pool.push_back(t.a); ev_pool.push_back(t.b); }
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (owns_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  // ------------------------------------------------------------- device budget (batch runs)
+  mps_status coop_ensure(int ctas) {
+    if (!shared_gpu || ctas <= 1 || ctas <= coop_held) return MPS_OK;
+    if (coop_held > 0) {
+      // this handle's earlier multi-CTA launches must finish before it returns their CTAs
+      if (mps_status s = cu(cudaStreamSynchronize(stream))) return s;
+      coop_release();
+    }
+    coop_budget(device).acquire(ctas, sm_count);
+    coop_held = std::min(ctas, sm_count);
+    return MPS_OK;
+  }
+  void coop_release() {
+    if (coop_held > 0) coop_budget(device).release(coop_held);
+    coop_held = 0;
   }
 
   cudaEvent_t ev_get() {
@@ -191,6 +249,7 @@ struct Engine final : mps_state {
     log_on = o.log_truncations != 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MPS_ERR_CUDA;
+    device = dev;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
     chi_cap = o.chi_max > 0 ? o.chi_max : kDefaultCap;
     if (o.fixed_chi > 0) chi_cap = std::min(chi_cap, o.fixed_chi);
@@ -234,11 +293,17 @@ struct Engine final : mps_state {
     site.resize(N);
     for (int i = 0; i < N; ++i) site[i] = arena + off[i];
     if (mps_status s = cu(cudaMemsetAsync(arena, 0, sizeof(Z) * total, stream))) return s;
-    // |0> (PURE) or vec(|0><0|) (MIXED, t = 0): entry [0, 0, 0] = 1 on every site
+    // |0> (PURE) or vec(|0><0|) (MIXED, t = 0): entry [0, 0, 0] = 1 on every site.  Every copy
+    // is ordered on the handle's stream behind the memset above (a copy on the legacy default
+    // stream is not ordered after work on a non-blocking stream); the final synchronisation
+    // keeps the host sources alive until the copies have run.
     std::vector<Z> ones(1, mk<R>(1, 0));
     for (int i = 0; i < N; ++i)
-      if (mps_status s = cu(cudaMemcpy(site[i], ones.data(), sizeof(Z), cudaMemcpyHostToDevice))) return s;
-    if (mps_status s = cu(cudaMemcpy(site_dev, site.data(), sizeof(Z*) * N, cudaMemcpyHostToDevice))) return s;
+      if (mps_status s = cu(cudaMemcpyAsync(site[i], ones.data(), sizeof(Z), cudaMemcpyHostToDevice, stream)))
+        return s;
+    if (mps_status s = cu(cudaMemcpyAsync(site_dev, site.data(), sizeof(Z*) * N, cudaMemcpyHostToDevice, stream)))
+      return s;
+    if (mps_status s = cu(cudaStreamSynchronize(stream))) return s;
     std::memset(hctrl, 0, sizeof(DevCtrl));
     hctrl->product = 1.0;
     hctrl->f_min = o.f_min;
@@ -301,6 +366,7 @@ struct Engine final : mps_state {
       plan = jacobi_plan<R>(l, c, acc, sm_count, fit);
       if (plan.nb / 2 > fit) return MPS_ERR_ARG;
     }
+    if (mps_status s = coop_ensure(plan.cluster > 0 ? plan.cluster : plan.nb / 2)) return s;
     ++n_jac;
     if (in_move) ++n_jac_move;
     const int id = tbegin();
@@ -313,6 +379,7 @@ struct Engine final : mps_state {
   mps_status read_ctrl() {
     if (mps_status s = cu(cudaMemcpyAsync(hctrl, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, stream))) return s;
     if (mps_status s = cu(cudaStreamSynchronize(stream))) return s;
+    coop_release();   // every launch of this handle has finished
     harvest();
     sticky |= hctrl->status & (ST_TIMEOUT | ST_NONFINITE | ST_NOT_CONVERGED | ST_BAD_ARG);
     return from_bits(sticky);
@@ -807,6 +874,73 @@ mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, co
     mps_status s = h->apply_2q(qs[g], ops_dev + (size_t)g * 2 * op_dim * op_dim, true, op_dim, target);
     if (s == MPS_WARN_CHI_CAP) { worst = s; continue; }
     if (s != MPS_OK) return s;
+  }
+  return worst;
+}
+
+mps_status mps_batch_run(mps_batch_item* items, int count, int concurrency, mps_handle* keep) {
+  if (count < 0 || (count > 0 && !items) || concurrency < 1) return MPS_ERR_ARG;
+  if (count == 0) return MPS_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPS_ERR_CUDA;
+  for (int i = 0; i < count; ++i) {
+    items[i].status = MPS_ERR_STATE;
+    items[i].fidelity = 0.0;
+    items[i].max_bond = 0;
+    if (keep) keep[i] = nullptr;
+  }
+  // longest circuits first (gates x qubits), so the tail of the batch is short work
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)items[a].n_gates * items[a].n_qubits > (long long)items[b].n_gates * items[b].n_qubits;
+  });
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      mps_batch_item& it = items[order[i]];
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { it.status = MPS_ERR_CUDA; continue; }
+      mps_handle h = nullptr;
+      mps_status s = mps_create(&h, it.n_qubits, &it.opt, st);
+      if (s != MPS_OK) {
+        cudaStreamDestroy(st);
+        it.status = s;
+        continue;
+      }
+      h->owns_stream = true;
+      h->shared_gpu = concurrency > 1;
+      s = mps_apply_circuit_device(h, it.n_gates, it.qs, it.ops_dev, it.op_dim, it.target);
+      if (s == MPS_OK || s == MPS_WARN_CHI_CAP) {
+        mps_status f = mps_fidelity(h, &it.fidelity);
+        if (f != MPS_OK) s = f;
+        int mx = 1;
+        for (int b = 1; b < h->N; ++b) mx = std::max(mx, h->bonds[b]);
+        it.max_bond = mx;
+      }
+      it.status = s;
+      if (keep) keep[order[i]] = h;
+      else mps_destroy(h);
+    }
+  };
+  const int nthreads = std::min(concurrency, count);
+  if (nthreads == 1) {
+    worker();
+  } else {
+    std::vector<std::thread> pool;
+    pool.reserve(nthreads);
+    for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+    for (std::thread& t : pool) t.join();
+  }
+  mps_status worst = MPS_OK;
+  for (int i = 0; i < count; ++i) {
+    const mps_status s = (mps_status)items[i].status;
+    if (s == MPS_OK) continue;
+    if (s == MPS_WARN_CHI_CAP) { if (worst == MPS_OK) worst = s; continue; }
+    if (worst == MPS_OK || worst == MPS_WARN_CHI_CAP) worst = s;
   }
   return worst;
 }

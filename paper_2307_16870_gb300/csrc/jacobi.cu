@@ -899,7 +899,7 @@ int rows_per_lane(int L) {
 template <class R>
 int jacobi_max_ctas(const JacobiPlan& plan) {
   const void* fn = plan.fn ? plan.fn : (const void*)jacobi_kernel<R>;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem) != cudaSuccess) return 0;
+  if (allow_dynamic_smem(fn) != cudaSuccess) return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, plan.threads, plan.smem) != cudaSuccess) return 0;
   int dev = 0, sms = 0;
@@ -1024,7 +1024,7 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
                           size_t xch_cap, unsigned* flags, int flags_cap, cudaStream_t st) {
   if (c <= 1) return cudaSuccess;   // a single column is already orthogonal
   if ((size_t)2 * plan.nb * plan.w * (size_t)plan.ld > xch_cap || plan.nb > flags_cap) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(plan.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+  cudaError_t e = allow_dynamic_smem(plan.fn);
   if (e != cudaSuccess) return e;
   // reset barrier and sweep counters (bar_count, bar_gen, rot[3] are contiguous) and the position flags
   e = cudaMemsetAsync(&ctrl->bar_count, 0, 5 * sizeof(unsigned), st);

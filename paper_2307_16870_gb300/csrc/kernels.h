@@ -13,6 +13,21 @@ namespace eamps {
 // unordered).  If W != nullptr the rotations are also applied to the c x c
 // matrix W (column j at W + j*ldw), which must hold the identity on entry, so
 // that W = V.  Cooperative launch; status bits and sweep count go to ctrl.
+// Allow `fn` the largest dynamic shared memory the device offers (opt-in maximum minus the
+// kernel's static shared memory).  Always the same value for a given kernel, so concurrent
+// host threads that launch it with different dynamic sizes cannot undo each other's setting.
+inline cudaError_t allow_dynamic_smem(const void* fn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 struct JacobiPlan {
   int w = 1;               // columns per block
   int nb = 2;              // number of blocks (even); CTAs = nb / 2

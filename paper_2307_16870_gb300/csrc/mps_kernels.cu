@@ -419,7 +419,7 @@ cudaError_t select_bond(const cplx<R>* Y, long long ldy, int l, int c, DevCtrl* 
   while (n2 < c) n2 <<= 1;
   if (n2 > 8192) return cudaErrorInvalidValue;
   size_t smem = (size_t)n2 * (2 * sizeof(double) + sizeof(int));
-  cudaError_t e = cudaFuncSetAttribute(select_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)select_kernel<R>);
   if (e != cudaSuccess) return e;
   select_kernel<R><<<1, 1024, smem, st>>>(Y, ldy, l, c, n2, ctrl, target, s_sorted, perm);
   return cudaGetLastError();

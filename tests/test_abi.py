@@ -65,3 +65,34 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     assert lib.mps_create(ctypes.byref(h), 4, ctypes.byref(o), None) == 1
     assert h.value is None
     assert lib.mps_destroy(None) == 0
+
+
+def test_batch_item_layout_matches_header(tmp_path):
+    """Field offsets of BatchItem against the C struct, compiled from the header."""
+    import shutil
+    import subprocess
+    import paper_2307_16870_gb300 as E
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    fields = ["n_qubits", "n_gates", "qs", "ops_dev", "op_dim", "target", "opt", "fidelity", "max_bond", "status"]
+    src = tmp_path / "off.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"eamps.h\"\nint main(void){\n" +
+                   "".join(f'  printf("%zu\\n", offsetof(mps_batch_item, {f}));\n' for f in fields) +
+                   '  printf("%zu\\n", sizeof(mps_batch_item));\n  return 0;\n}\n')
+    exe = tmp_path / "off"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [getattr(E.BatchItem, f).offset for f in fields] + [ctypes.sizeof(E.BatchItem)]
+    assert got == want
+
+
+def test_batch_rejects_bad_arguments_without_touching_the_gpu():
+    import paper_2307_16870_gb300 as E
+    lib = E.load()
+    items = (E.BatchItem * 1)()
+    assert lib.mps_batch_run(items, -1, 1, None) == 1
+    assert lib.mps_batch_run(None, 2, 1, None) == 1
+    assert lib.mps_batch_run(items, 1, 0, None) == 1
+    assert lib.mps_batch_run(items, 0, 4, None) == 0
