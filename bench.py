@@ -59,10 +59,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
-    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch"],
+    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies"],
                     help="ttf: time to target fidelity, EA against fixed bond dimensions; "
                          "mpo: the noisy EA-MPO workload (d = 4); "
-                         "batch: 64 independent circuits run concurrently")
+                         "batch: 64 independent circuits run concurrently; "
+                         "strategies: inferred vs true fidelity of the naive/global/nearest schedules")
     ap.add_argument("--micro", type=int, default=0, metavar="CHI",
                     help="instead of the circuit: a few two-site updates on a random canonical 24-site MPS "
                          "with every bond CHI (the launch configuration of the circuit's saturated gates)")
@@ -359,7 +360,9 @@ def run_study(a) -> int:
     p = 0.01 and amplitude damping gamma = 0.005 on both qubits, F_min = 0.95.
     batch: 64 independent brickworks (N ~ U[20, 80], depth ~ U[10, 30], F_min in
     {0.9, 0.99}, bond cap 128) through mps_batch_run at concurrency 1, 4, 8, 16;
-    wall time of the whole batch (host threads included).
+    wall time of the whole batch (host threads included).  strategies: an 18-qubit
+    depth-18 brickwork at F_min 0.9 and 0.5 under each schedule; the true
+    fidelity |<exact|EA>|^2 comes from mps_overlap with the untruncated run.
     """
     import torch
     import paper_2307_16870_gb300 as E
@@ -414,6 +417,35 @@ def run_study(a) -> int:
                       "f_min": 0.95, "mixed_fid": "kept_ratio" if mixed_fid == E.KEPT_RATIO else "wang_sqrt",
                       "chi_cap": cap, "gpu_s": ms / 1e3, "updates_per_s": n / (ms / 1e3),
                       "inferred_fidelity": fid, "max_bond": mx, "jacobi_share": jms / ms})
+    elif a.study == "strategies":
+        n_q, depth = 18, 18
+        circ = W.brickwork_circuit(n_q, depth, a.seed)
+        n = circ.n_2q
+        ops_dev = torch.from_numpy(circ.ops_array().view(np.float64).reshape(n, 32).copy()).to(dev)
+        qs = np.asarray(circ.qs, dtype=np.int32)
+        exact = E.MPS(n_q, n_2q=n, precision=prec, log_truncations=False)
+        E.mps_apply_circuit_device(exact.h, qs, ops_dev.data_ptr(), 4, 1.0)     # untruncated reference
+        names = {E.NAIVE: "naive", E.GLOBAL: "global", E.NEAREST: "nearest"}
+        for f_min in (0.9, 0.5):
+            for strat in (E.NAIVE, E.GLOBAL, E.NEAREST):
+                stream = torch.cuda.current_stream(dev)
+                m = E.MPS(n_q, f_min=f_min, n_2q=n, strategy=strat, precision=prec, log_truncations=False,
+                          stream=stream.cuda_stream)
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                E.mps_apply_circuit_device(m.h, qs, ops_dev.data_ptr(), 4)
+                inferred = m.fidelity()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                true_f = abs(exact.overlap(m)) ** 2
+                emit({"study": "strategies", "n_qubits": n_q, "depth": depth, "n_2q": n, "f_min": f_min,
+                      "strategy": names[strat], "inferred_fidelity": inferred, "true_fidelity": true_f,
+                      "gpu_s": e0.elapsed_time(e1) / 1e3, "max_bond": max(m.bond_dims()),
+                      "exact_max_bond": max(exact.bond_dims())})
+                m.close()
+        exact.close()
     elif a.study == "batch":
         specs = W.random_batch_specs(64, a.seed)
         cap = 128

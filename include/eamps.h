@@ -180,6 +180,19 @@ mps_status mps_batch_run(mps_batch_item* items, int count, int concurrency, mps_
 /* *inferred = running product of truncation fidelities (Eq. prod), FP64. */
 mps_status mps_fidelity(mps_handle h, double* inferred);
 
+/* <a|b>: the inner product of two handles of the same length and kind
+ * ("The matrix product formalism" section: the overlap of two MPS is the
+ * chain of transfer contractions E <- sum_s A_s^dagger E B_s).  PURE: the
+ * state overlap (|<a|b>|^2 is the true fidelity of Eq. F-pure when one
+ * handle holds the exact state).  MIXED: the Hilbert-Schmidt inner product
+ * Tr(rho_a^dagger rho_b) of the vectorised operators.  Both handles' norm
+ * factors (the FP64 log-norms) are included.  Computed in FP64 on a's
+ * stream after the pending work of both handles; the bonds and precisions of
+ * a and b may differ.  Allocates its FP64 workspace for the call.
+ * out_re_im: host, 2 doubles.  Errors: MPS_ERR_ARG (NULL, different lengths
+ * or kinds), MPS_ERR_OOM, MPS_ERR_CUDA, or a sticky error of either handle. */
+mps_status mps_overlap(mps_handle a, mps_handle b, double* out_re_im);
+
 /* PURE: <psi|O|psi>, computed from the canonical form with only the tensors
  * on the support ("Canonicalization" section; the centre is moved onto the
  * support).  MIXED: Tr(O rho)/Tr(rho) by a transfer contraction along the

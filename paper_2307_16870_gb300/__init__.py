@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-from .build import LIB, build
+from .build import LIB, _stale, build
 
 __all__ = [
     "PURE", "MIXED", "NAIVE", "GLOBAL", "NEAREST", "FP64", "TF32X3", "FP32", "KEPT_RATIO", "WANG_SQRT",
@@ -26,7 +26,7 @@ __all__ = [
     "mps_bond_dims", "mps_centre", "mps_get_site", "mps_lognorm", "mps_last_singular_values",
     "mps_truncation_log", "mps_sync", "mps_superop_from_kraus", "mps_status_string",
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
-    "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run",
+    "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap",
 ]
 
 PURE, MIXED = 0, 1
@@ -75,13 +75,13 @@ _lib = None
 
 
 def load(path: str | None = None):
-    """Load libeamps.so (building it first if it is missing)."""
+    """Load libeamps.so (building it first if it is missing or older than its sources)."""
     global _lib
     if _lib is not None:
         return _lib
     path = path or LIB
-    if not os.path.exists(path):
-        build()
+    if not os.path.exists(path) or (path == LIB and _stale([])):
+        build()     # missing, or older than a source or header
     lib = C.CDLL(path)
     H = C.c_void_p
     D = C.POINTER(C.c_double)
@@ -118,6 +118,7 @@ def load(path: str | None = None):
         "mps_stats": (C.c_int, [H, C.POINTER(MpsStats)]),
         "mps_stats_reset": (C.c_int, [H]),
         "mps_batch_run": (C.c_int, [C.POINTER(BatchItem), C.c_int, C.c_int, C.POINTER(H)]),
+        "mps_overlap": (C.c_int, [H, H, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +190,12 @@ def mps_apply_circuit_device(h: int, qs, ops_dev_ptr: int, op_dim: int, target: 
     return _check(load().mps_apply_circuit_device(C.c_void_p(h), int(q.size), q.ctypes.data_as(C.POINTER(C.c_int)),
                                                   C.c_void_p(ops_dev_ptr), int(op_dim), float(target)),
                   "mps_apply_circuit_device")
+
+
+def mps_overlap(a: int, b: int) -> complex:
+    out = np.zeros(2)
+    _check(load().mps_overlap(C.c_void_p(a), C.c_void_p(b), _dptr(out)), "mps_overlap")
+    return complex(out[0], out[1])
 
 
 def mps_fidelity(h: int) -> float:
@@ -400,6 +407,10 @@ class MPS:
 
     def fidelity(self):
         return mps_fidelity(self.h)
+
+    def overlap(self, other: "MPS") -> complex:
+        """<self|other> (MIXED: Tr(rho_self^dagger rho_other)), FP64."""
+        return mps_overlap(self.h, other.h)
 
     def expect(self, q, op):
         return mps_expect(self.h, q, op)

@@ -110,6 +110,8 @@ struct mps_state {
   virtual mps_status profile(int on) = 0;
   virtual mps_status stats(mps_stats_t* out) = 0;
   virtual mps_status stats_reset() = 0;
+  // site i (bonds[i] x d x bonds[i+1], row-major) converted to FP64 into dst, ordered on st
+  virtual mps_status site_to_double(int i, double2* dst, cudaStream_t st) = 0;
   int N = 0;
   int d = 2;
   int centre = 0;
@@ -584,6 +586,11 @@ struct Engine final : mps_state {
     return s;
   }
 
+  mps_status site_to_double(int i, double2* dst, cudaStream_t st) override {
+    if (i < 0 || i >= N || !dst) return MPS_ERR_ARG;
+    return kl(to_double<R>(site[i], dst, (long long)bonds[i] * d * bonds[i + 1], st));
+  }
+
   mps_status lognorm(double* out) override {
     mps_status s = read_ctrl();
     *out = hctrl->lognorm;
@@ -943,6 +950,61 @@ mps_status mps_batch_run(mps_batch_item* items, int count, int concurrency, mps_
     if (worst == MPS_OK || worst == MPS_WARN_CHI_CAP) worst = s;
   }
   return worst;
+}
+
+mps_status mps_overlap(mps_handle a, mps_handle b, double* out_re_im) {
+  if (!a || !b || !out_re_im || a->N != b->N || a->d != b->d) return MPS_ERR_ARG;
+  // finish and check the pending work of both handles (and read their log-norms)
+  double la = 0.0, lb = 0.0;
+  if (mps_status s = a->lognorm(&la)) return s;
+  if (mps_status s = b->lognorm(&lb)) return s;
+  const int N = a->N, d = a->d;
+  int xa = 1, xb = 1;
+  size_t sa = 1, sb = 1;
+  for (int i = 0; i < N; ++i) {
+    xa = std::max(xa, a->bonds[i + 1]);
+    xb = std::max(xb, b->bonds[i + 1]);
+    sa = std::max(sa, (size_t)a->bonds[i] * d * a->bonds[i + 1]);
+    sb = std::max(sb, (size_t)b->bonds[i] * d * b->bonds[i + 1]);
+  }
+  cudaStream_t st = a->stream;
+  double2 *E = nullptr, *T = nullptr, *SA = nullptr, *SB = nullptr;
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    for (double2* p : {E, T, SA, SB}) if (p) cudaFree(p);
+  };
+  if (cudaMalloc(&E, sizeof(double2) * (size_t)xa * xb) != cudaSuccess ||
+      cudaMalloc(&T, sizeof(double2) * (size_t)xa * d * xb) != cudaSuccess ||
+      cudaMalloc(&SA, sizeof(double2) * sa) != cudaSuccess || cudaMalloc(&SB, sizeof(double2) * sb) != cudaSuccess) {
+    release();
+    return MPS_ERR_OOM;
+  }
+  const double2 one = make_double2(1.0, 0.0);
+  mps_status s = MPS_OK;
+  auto ck = [&](cudaError_t e) { if (e != cudaSuccess && s == MPS_OK) s = MPS_ERR_CUDA; return s == MPS_OK; };
+  ck(cudaMemcpyAsync(E, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
+  // transfer contraction: E (cla x clb) -> E' (cra x crb) = sum_s A_s^dagger E B_s
+  for (int i = 0; i < N && s == MPS_OK; ++i) {
+    const int cla = a->bonds[i], cra = a->bonds[i + 1], clb = b->bonds[i], crb = b->bonds[i + 1];
+    if ((s = a->site_to_double(i, SA, st)) != MPS_OK) break;
+    if ((s = b->site_to_double(i, SB, st)) != MPS_OK) break;
+    // T[(alpha, s), beta'] = sum_beta E[alpha, beta] B[beta, s, beta']
+    for (int t = 0; t < d && s == MPS_OK; ++t)
+      ck(cgemm_simt<double>(cla, crb, clb, 1.0, E, clb, 1, 0, SB + (size_t)t * crb, (long long)d * crb, 1, 0,
+                            T + (size_t)t * crb, (long long)d * crb, 1, st));
+    // E'[alpha', beta'] = sum_{(alpha, s)} conj(A[(alpha, s), alpha']) T[(alpha, s), beta']
+    if (s == MPS_OK)
+      ck(cgemm_simt<double>(cra, crb, cla * d, 1.0, SA, 1, cra, 1, T, crb, 1, 0, E, crb, 1, st));
+  }
+  double2 r = make_double2(0.0, 0.0);
+  if (s == MPS_OK) ck(cudaMemcpyAsync(&r, E, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  if (s == MPS_OK) ck(cudaStreamSynchronize(st));
+  release();
+  if (s != MPS_OK) return s;
+  const double scale = std::exp(la + lb);
+  out_re_im[0] = r.x * scale;
+  out_re_im[1] = r.y * scale;
+  return MPS_OK;
 }
 
 mps_status mps_fidelity(mps_handle h, double* inferred) {
