@@ -180,6 +180,18 @@ mps_status mps_batch_run(mps_batch_item* items, int count, int concurrency, mps_
 /* *inferred = running product of truncation fidelities (Eq. prod), FP64. */
 mps_status mps_fidelity(mps_handle h, double* inferred);
 
+/* Householder QR of an l x c complex64 matrix in DEVICE memory, the
+ * factorisation that brings a site into canonical form ("Canonicalization"
+ * section): X = Q R.  X: column-major, leading dimension ldx >= l, factored
+ * in place (R, min(l, c) x c upper trapezoid with a real diagonal, in the
+ * upper part; the Householder vectors, unit leading entry implicit, below).
+ * Q: NULL, or DEVICE column-major l x min(l, c) (ldq >= l) receiving the
+ * factor with orthonormal columns.  l <= 512.  Runs on `stream` (NULL: the
+ * default stream) and synchronises it; allocates its workspace for the call.
+ * Errors: MPS_ERR_ARG (sizes, NULL X), MPS_ERR_OOM, MPS_ERR_CUDA,
+ * MPS_ERR_TIMEOUT (a bounded device barrier gave up). */
+mps_status mps_qr_c64(int l, int c, void* X, long long ldx, void* Q, long long ldq, void* stream);
+
 /* <a|b>: the inner product of two handles of the same length and kind
  * ("The matrix product formalism" section: the overlap of two MPS is the
  * chain of transfer contractions E <- sum_s A_s^dagger E B_s).  PURE: the

@@ -26,7 +26,7 @@ __all__ = [
     "mps_bond_dims", "mps_centre", "mps_get_site", "mps_lognorm", "mps_last_singular_values",
     "mps_truncation_log", "mps_sync", "mps_superop_from_kraus", "mps_status_string",
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
-    "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap",
+    "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap", "mps_qr_c64",
 ]
 
 PURE, MIXED = 0, 1
@@ -119,6 +119,7 @@ def load(path: str | None = None):
         "mps_stats_reset": (C.c_int, [H]),
         "mps_batch_run": (C.c_int, [C.POINTER(BatchItem), C.c_int, C.c_int, C.POINTER(H)]),
         "mps_overlap": (C.c_int, [H, H, D]),
+        "mps_qr_c64": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p, C.c_longlong, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -190,6 +191,12 @@ def mps_apply_circuit_device(h: int, qs, ops_dev_ptr: int, op_dim: int, target: 
     return _check(load().mps_apply_circuit_device(C.c_void_p(h), int(q.size), q.ctypes.data_as(C.POINTER(C.c_int)),
                                                   C.c_void_p(ops_dev_ptr), int(op_dim), float(target)),
                   "mps_apply_circuit_device")
+
+
+def mps_qr_c64(l: int, c: int, x_ptr: int, ldx: int, q_ptr: int = 0, ldq: int = 0, stream: int = 0) -> int:
+    """In-place Householder QR of a device complex64 matrix (see include/eamps.h)."""
+    return _check(load().mps_qr_c64(int(l), int(c), C.c_void_p(x_ptr), int(ldx), C.c_void_p(q_ptr or None),
+                                    int(ldq), C.c_void_p(stream or None)), "mps_qr_c64")
 
 
 def mps_overlap(a: int, b: int) -> complex:

@@ -952,6 +952,35 @@ mps_status mps_batch_run(mps_batch_item* items, int count, int concurrency, mps_
   return worst;
 }
 
+mps_status mps_qr_c64(int l, int c, void* X, long long ldx, void* Q, long long ldq, void* stream) {
+  if (l < 1 || c < 1 || !X || ldx < l || l > qr_max_rows() || (Q && ldq < l)) return MPS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int K = std::min(l, c), npan = (K + 31) / 32;
+  float2 *tau = nullptr, *Tm = nullptr;
+  DevCtrl* ctrl = nullptr;
+  auto release = [&]() {
+    if (tau) cudaFree(tau);
+    if (Tm) cudaFree(Tm);
+    if (ctrl) cudaFree(ctrl);
+  };
+  if (cudaMalloc(&tau, sizeof(float2) * K) != cudaSuccess || cudaMalloc(&Tm, sizeof(float2) * 1024 * npan) != cudaSuccess ||
+      cudaMalloc(&ctrl, sizeof(DevCtrl)) != cudaSuccess) {
+    release();
+    return MPS_ERR_OOM;
+  }
+  const int fit = qr_max_ctas();
+  const int ctas = qr_ctas(l, c, std::max(1, fit));
+  cudaError_t err = cudaMemsetAsync(ctrl, 0, sizeof(DevCtrl), st);
+  if (err == cudaSuccess) err = qr_factor((float2*)X, ldx, l, c, tau, Tm, ctrl, ctas, st);
+  if (err == cudaSuccess && Q) err = qr_form_q((const float2*)X, ldx, l, c, Tm, (float2*)Q, ldq, ctrl, qr_ctas(l, K, std::max(1, fit)), st);
+  int status = 0;
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&status, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  release();
+  if (err != cudaSuccess) return MPS_ERR_CUDA;
+  return from_bits(status);
+}
+
 mps_status mps_overlap(mps_handle a, mps_handle b, double* out_re_im) {
   if (!a || !b || !out_re_im || a->N != b->N || a->d != b->d) return MPS_ERR_ARG;
   // finish and check the pending work of both handles (and read their log-norms)

@@ -28,6 +28,19 @@ inline cudaError_t allow_dynamic_smem(const void* fn) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
+// Householder QR of the l x c complex64 matrix X (column-major, leading dimension ldx), in place:
+// R in the upper trapezoid, the reflector vectors (unit leading entry implicit) below the
+// diagonal, tau (min(l, c) entries) and the block-reflector factors Tm (32 x 32 per panel of
+// 32 columns).  Rows l <= qr_max_rows().  ctas > 1: cooperative launch (at most qr_max_ctas()).
+int qr_max_rows();
+int qr_max_ctas();
+int qr_ctas(int l, int c, int max_ctas);
+cudaError_t qr_factor(float2* X, long long ldx, int l, int c, float2* tau, float2* Tm, DevCtrl* ctrl, int ctas,
+                      cudaStream_t st);
+// Q (l x min(l, c), column-major, leading dimension ldq) from the reflectors left by qr_factor.
+cudaError_t qr_form_q(const float2* X, long long ldx, int l, int c, const float2* Tm, float2* Q, long long ldq,
+                      DevCtrl* ctrl, int ctas, cudaStream_t st);
+
 struct JacobiPlan {
   int w = 1;               // columns per block
   int nb = 2;              // number of blocks (even); CTAs = nb / 2

@@ -1,0 +1,73 @@
+"""Householder QR kernels (mps_qr_c64) against the definition X = Q R, Q^dagger Q = I,
+R upper triangular, and against LAPACK's R (same real-diagonal convention)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+E = pytest.importorskip("paper_2307_16870_gb300")
+
+
+def _rand(l, c, seed, graded=False):
+    g = np.random.default_rng(seed)
+    x = (g.normal(size=(l, c)) + 1j * g.normal(size=(l, c))) / np.sqrt(2)
+    if graded:      # singular values spanning 1 .. e^-10
+        u, _ = np.linalg.qr(x)
+        v, _ = np.linalg.qr(g.normal(size=(c, c)) + 1j * g.normal(size=(c, c)))
+        k = min(l, c)
+        x = (u[:, :k] * np.exp(-np.linspace(0, 10, k))) @ v[:k, :]
+    return x.astype(np.complex64)
+
+
+def _qr_gpu(x):
+    l, c = x.shape
+    k = min(l, c)
+    xd = torch.from_numpy(np.asfortranarray(x).T.copy()).cuda()          # column-major: row j = column j
+    qd = torch.zeros((k, l), dtype=torch.complex64, device="cuda")
+    E.mps_qr_c64(l, c, xd.data_ptr(), l, qd.data_ptr(), l)
+    f = xd.cpu().numpy().T                                               # factored, l x c
+    q = qd.cpu().numpy().T                                               # l x k
+    r = np.triu(f[:k, :])
+    return q.astype(np.complex128), r.astype(np.complex128)
+
+
+SHAPES = [(1, 1), (7, 3), (32, 32), (33, 31), (64, 96), (100, 40), (256, 256), (300, 129), (512, 256),
+          (512, 512), (480, 500), (512, 37)]
+
+
+@pytest.mark.parametrize("l,c", SHAPES)
+def test_qr_definition(l, c):
+    x = _rand(l, c, l * 1000 + c)
+    q, r = _qr_gpu(x)
+    x64 = x.astype(np.complex128)
+    nx = np.linalg.norm(x64)
+    assert np.linalg.norm(q @ r - x64) < 2e-6 * nx * np.sqrt(max(l, c) / 32)
+    k = min(l, c)
+    assert np.abs(q.conj().T @ q - np.eye(k)).max() < 3e-6 * np.sqrt(l / 32)
+    assert np.all(np.abs(np.imag(np.diag(r))) < 1e-6 * np.abs(np.diag(r)).max())   # real diagonal
+    # LAPACK's R (numpy) has the same convention: equal up to rounding
+    _, r_ref = np.linalg.qr(x64, mode="reduced" if l >= c else "complete")
+    r_ref = r_ref[:k, :]
+    assert np.abs(r - r_ref).max() < 5e-6 * np.abs(r_ref).max() * np.sqrt(max(l, c) / 32)
+
+
+def test_qr_graded_and_rank_deficient():
+    x = _rand(512, 512, 5, graded=True)
+    q, r = _qr_gpu(x)
+    x64 = x.astype(np.complex128)
+    assert np.linalg.norm(q @ r - x64) < 1e-5 * np.linalg.norm(x64)
+    assert np.abs(q.conj().T @ q - np.eye(512)).max() < 1e-5
+    # exact zero columns and a rank-one block
+    z = np.zeros((64, 48), np.complex64)
+    z[:, 5] = _rand(64, 1, 9)[:, 0]
+    z[:, 20] = 2 * z[:, 5]
+    q, r = _qr_gpu(z)
+    assert np.linalg.norm(q @ r - z) < 1e-5 * np.linalg.norm(z)
+    assert np.abs(q.conj().T @ q - np.eye(48)).max() < 1e-5
+
+
+def test_qr_rejects_too_many_rows():
+    x = torch.zeros((4, 513), dtype=torch.complex64, device="cuda")
+    with pytest.raises(E.MpsError):
+        E.mps_qr_c64(513, 4, x.data_ptr(), 513)
