@@ -302,6 +302,8 @@ def run_ours(a) -> int:
             "launches": st["jacobi_launches"], "avg_launch_ms": st["jacobi_ms"] / max(st["jacobi_launches"], 1),
             "sweeps_per_launch": st["jacobi_sweeps"] / max(st["jacobi_launches"], 1),
             "centre_move_share": (st["move_jacobi_ms"] / st["jacobi_ms"]) if st["jacobi_ms"] else None}
+    qr = {"launches": st["qr_launches"], "ms": st["qr_ms"],
+          "share_of_step": (st["qr_ms"] / sum(step_ms)) if step_ms else None}
     gemm = {"launches": st["gemm_launches"], "ms": st["gemm_ms"],
             "tflops": (st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12) if st["gemm_ms"] > 0 else None}
     cpu = None
@@ -320,7 +322,7 @@ def run_ours(a) -> int:
                            "parallelism": "replicas" if world > 1 else "single"},
                 "inferred_fidelity": fid, "final_max_bond": max(bonds),
                 "wall_s_timed": wall, "gpu_launches": st["kernel_launches"], "roofline": roof,
-                "contraction": gemm, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
+                "contraction": gemm, "householder_qr": qr, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
         print(json.dumps(line), flush=True)
     m.close()
     if world > 1:
@@ -496,6 +498,7 @@ def run_micro(a) -> int:
     st = m.stats()
     jl = max(st["jacobi_launches"], 1)
     print(json.dumps({"micro_chi": chi, "jacobi_ms_per_launch": st["jacobi_ms"] / jl,
+                      "qr_ms_per_launch": st["qr_ms"] / max(st["qr_launches"], 1),
                       "sweeps_per_launch": st["jacobi_sweeps"] / jl,
                       "jacobi_tflops": st["jacobi_flops"] / (st["jacobi_ms"] / 1e3) / 1e12 if st["jacobi_ms"] else None}))
     m.close()

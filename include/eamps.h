@@ -269,13 +269,17 @@ typedef struct {
   long long jacobi_launches;
   long long jacobi_sweeps;     /* sweeps summed over launches */
   double jacobi_ms;            /* summed event durations (profiling on) */
-  double jacobi_flops;         /* algorithmic FP flops of the Jacobi launches (see DESIGN) */
+  double jacobi_flops;         /* algorithmic flops of the Jacobi launches: 16 l per visited pair
+                                  (three complex inner products over l rows) + 24 L per applied
+                                  rotation (two complex column updates of L rows) */
   long long gemm_launches;
   double gemm_ms;
   double gemm_flops;           /* 8 M N K per complex GEMM */
   long long gates;             /* two-qubit updates applied */
   long long move_jacobi_launches;  /* Jacobi launches of centre moves (included in jacobi_*) */
   double move_jacobi_ms;           /* their summed event durations (profiling on) */
+  long long qr_launches;           /* Householder QR launches (centre moves and SVD preconditioning) */
+  double qr_ms;                    /* their summed event durations (profiling on) */
 } mps_stats_t;
 
 /* Switch event timing of the Jacobi and contraction launches on (1) or off (0). */

@@ -62,7 +62,8 @@ class MpsStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_longlong), ("jacobi_launches", C.c_longlong),
                 ("jacobi_sweeps", C.c_longlong), ("jacobi_ms", C.c_double), ("jacobi_flops", C.c_double),
                 ("gemm_launches", C.c_longlong), ("gemm_ms", C.c_double), ("gemm_flops", C.c_double),
-                ("gates", C.c_longlong), ("move_jacobi_launches", C.c_longlong), ("move_jacobi_ms", C.c_double)]
+                ("gates", C.c_longlong), ("move_jacobi_launches", C.c_longlong), ("move_jacobi_ms", C.c_double),
+                ("qr_launches", C.c_longlong), ("qr_ms", C.c_double)]
 
 
 class MpsError(RuntimeError):

@@ -155,9 +155,15 @@ struct Engine final : mps_state {
   static constexpr int kFlagsCap = 4096;
   size_t site_cap = 0;
   TcGemm* tc = nullptr;
+  // Householder QR (complex64): centre moves and SVD preconditioning for <= qr_max_rows() rows
+  Z* qr_tau = nullptr;
+  Z* qr_T = nullptr;
+  int qr_fit = 0;
+  bool qr_on = false;
+  int qr_mode = 2;
   // statistics
-  long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0, n_jac_move = 0;
-  double gemm_flops = 0.0, jac_ms = 0.0, gemm_ms = 0.0, jac_move_ms = 0.0;
+  long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0, n_jac_move = 0, n_qr = 0;
+  double gemm_flops = 0.0, jac_ms = 0.0, gemm_ms = 0.0, jac_move_ms = 0.0, qr_ms_sum = 0.0;
   bool in_move = false;
   bool prof = false;
   struct Timed { cudaEvent_t a, b; int kind; };
@@ -168,7 +174,7 @@ struct Engine final : mps_state {
     if (stream) cudaStreamSynchronize(stream);
     coop_release();
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
-                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags};
+                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T};
     for (void* b : bufs) if (b) cudaFree(b);
     if (hctrl) cudaFreeHost(hctrl);
     if (hout) cudaFreeHost(hout);
@@ -220,6 +226,7 @@ struct Engine final : mps_state {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
         if (t.kind == 1) gemm_ms += ms;
+        else if (t.kind == 3) qr_ms_sum += ms;
         else {
           jac_ms += ms;
           if (t.kind == 2) jac_move_ms += ms;
@@ -322,6 +329,16 @@ struct Engine final : mps_state {
       tc = tc_create(big);
       if (!tc) return MPS_ERR_OOM;
     }
+    if (std::is_same<R, float>::value) {
+      // EAMPS_QR: 0 off, 1 the preconditioned gate SVD only, 2 also the centre moves (default)
+      const char* env = std::getenv("EAMPS_QR");
+      qr_mode = (env && *env) ? std::atoi(env) : 2;
+      qr_on = qr_mode > 0;
+      qr_fit = qr_on ? qr_max_ctas() : 0;
+      if (qr_fit <= 0) qr_on = false;
+      if (qr_on && (!dalloc(&qr_tau, (size_t)c_max) || !dalloc(&qr_T, (size_t)1024 * ((c_max + 31) / 32))))
+        return MPS_ERR_OOM;
+    }
     return MPS_OK;
   }
 
@@ -378,6 +395,27 @@ struct Engine final : mps_state {
     return s;
   }
 
+  // ------------------------------------------------------------- Householder QR
+  bool qr_ok(int rows, int cols) const { return qr_on && rows <= qr_max_rows() && rows >= 1 && cols >= 1; }
+
+  // X (l x c, column-major, ld ldx) = Q R in place; with Q != nullptr also the explicit Q
+  // (l x min(l, c), column-major, ld ldq).
+  mps_status qr_run(int l, int c, Z* Xp, long long ldx, Z* Q, long long ldq) {
+    if constexpr (std::is_same<R, float>::value) {
+      const int ctas = qr_ctas(l, c, qr_fit);
+      if (mps_status s = coop_ensure(ctas)) return s;
+      ++n_qr;
+      const int id = tbegin();
+      mps_status s = kl(qr_factor(Xp, ldx, l, c, qr_tau, qr_T, ctrl, ctas, stream));
+      if (s == MPS_OK && Q) s = kl(qr_form_q(Xp, ldx, l, c, qr_T, Q, ldq, ctrl, qr_ctas(l, std::min(l, c), qr_fit), stream));
+      tend(id, 3);
+      return s;
+    } else {
+      (void)l; (void)c; (void)Xp; (void)ldx; (void)Q; (void)ldq;
+      return MPS_ERR_ARG;
+    }
+  }
+
   mps_status read_ctrl() {
     if (mps_status s = cu(cudaMemcpyAsync(hctrl, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, stream))) return s;
     if (mps_status s = cu(cudaStreamSynchronize(stream))) return s;
@@ -397,7 +435,17 @@ struct Engine final : mps_state {
     Z* C = site[c];
     Z* Nx = site[c + 1];
     mps_status s;
-    if (n <= m) {
+    if (qr_mode >= 2 && qr_ok(m, n)) {
+      // C (m x n) = Q R: A_c <- Q (m x K), A_{c+1} <- R A_{c+1} (K x n2), bond K = min(m, n)
+      const int K = std::min(m, n);
+      if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;       // X = C column-major
+      if ((s = qr_run(m, n, X, m, Wacc, m))) return s;                                     // Q column-major
+      if ((s = kl(triu_extract<R>(tmp2, n, 1, X, m, K, n, 0, stream)))) return s;           // R row-major K x n
+      if ((s = gemm(K, n2, n, R(1), tmp2, n, 1, 0, Nx, n2, 1, 0, T, n2, 1))) return s;     // R A_{c+1}
+      if ((s = copy(Nx, T, (size_t)K * n2))) return s;
+      if ((s = extract(C, 1, K, K, m, Wacc, m, 1, nullptr, 0, nullptr, 0))) return s;      // A_c = Q row-major
+      bonds[c + 1] = K;
+    } else if (n <= m) {
       // X = C column-major; C W = Y; Q = Y/|Y| (m x n), R = Q^dagger C, A_{c+1} <- R A_{c+1}
       if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;
       if ((s = run_jacobi(m, n, false, X, m))) return s;
@@ -429,7 +477,19 @@ struct Engine final : mps_state {
     Z* C = site[c];
     Z* Pv = site[c - 1];
     mps_status s;
-    if (m <= n) {
+    if (qr_mode >= 2 && qr_ok(n, m)) {
+      // C^dagger (n x m) = Q R, so C = R^dagger Q^dagger: A_c <- Q^dagger (K x n),
+      // A_{c-1} <- A_{c-1} R^dagger (m2 x K), bond K = min(m, n)
+      const int K = std::min(m, n);
+      if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;        // X = C^dagger
+      if ((s = qr_run(n, m, X, n, Wacc, n))) return s;                                     // Q column-major n x K
+      if ((s = kl(triu_extract<R>(tmp2, m, 1, X, n, K, m, 0, stream)))) return s;           // R row-major K x m
+      if ((s = gemm(m2, K, m, R(1), Pv, m, 1, 0, tmp2, 1, m, 1, T, K, 1))) return s;       // A_{c-1} R^dagger
+      if ((s = copy(Pv, T, (size_t)m2 * K))) return s;
+      // Q^dagger row-major (K x n): element (r, j) = conj(Q(j, r)) sits where Q(j, r) sits
+      if ((s = extract(C, n, 1, K, n, Wacc, n, 1, nullptr, 1, nullptr, 0))) return s;
+      bonds[c] = K;
+    } else if (m <= n) {
       // X = C^dagger; C^dagger W = Y -> C = (W S) Yn^dagger: Q' = Yn^dagger (m x n), L = C Q'^dagger
       if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;
       if ((s = run_jacobi(n, m, false, X, n))) return s;
@@ -526,17 +586,33 @@ struct Engine final : mps_state {
     enum { R_COLS, R_ROWS_ACC, L_ROWS, L_COLS_ACC } mode;
     if (right) mode = (n <= m) ? R_COLS : R_ROWS_ACC;
     else mode = (m <= n) ? L_ROWS : L_COLS_ACC;
-    const bool cols = (mode == R_COLS || mode == L_COLS_ACC);     // X = theta (else theta^dagger)
+    // QR preconditioning when the wanted directions are the right singular vectors of a tall X:
+    // X = theta^dagger (n >= m) for a rightward update, X = theta (m >= n) for a leftward one
+    const bool use_qr = std::min(m, n) >= 2 && (right ? n >= m : m >= n) && qr_ok(std::max(m, n), std::min(m, n));
+    const bool cols = use_qr ? !right : (mode == R_COLS || mode == L_COLS_ACC);   // X = theta (else theta^dagger)
     const int l = cols ? m : n, c = cols ? n : m;
     if ((s = kl(gate_theta<R>(T, cl, d, cr, G, X, cols ? 0 : 1, theta, stream)))) return s;
-    // (a2) SVD: one-sided Jacobi gives the singular directions
+    // (a2) SVD: one-sided Jacobi gives the singular directions D with unit columns (FP64
+    // norms): left vectors U (m x c) for a rightward update, right vectors V (n x c) for a
+    // leftward one.  X (l x c, l >= c) is theta or theta^dagger.
     const bool acc = (mode == R_ROWS_ACC || mode == L_COLS_ACC);
-    if ((s = run_jacobi(l, c, acc, X, l))) return s;
-    // Directions D with unit columns (FP64 norms): left vectors U (m x c) for a rightward
-    // update, right vectors V (n x c) for a leftward one; from the rotated columns, or from
-    // the accumulated rotations when the Jacobi ran on the other side.
     const bool u_type = right;
-    {
+    if (use_qr) {
+      // Preconditioned: X = Q R, one-sided Jacobi on Y = R^dagger (c x c, column-major in Wacc);
+      // the rotated, normalised columns of Y are the right singular vectors of X: U when X is
+      // theta^dagger (rightward, c = m), V when X is theta (leftward, c = n).  They are
+      // orthonormal to the Jacobi tolerance whatever their singular values.
+      if ((s = qr_run(l, c, X, l, nullptr, 0))) return s;
+      if ((s = kl(triu_extract<R>(Wacc, c, 1, X, l, c, c, 1, stream)))) return s;
+      if ((s = run_jacobi(c, c, false, Wacc, c))) return s;
+      if ((s = kl(column_norms<R>(Wacc, c, c, c, norms, stream)))) return s;
+      if (u_type) s = extract(tmp, 1, c, c, m, Wacc, c, 1, nullptr, 0, norms, 0);   // U row-major (m x c)
+      else s = extract(tmp, n, 1, c, n, Wacc, c, 1, nullptr, 0, norms, 0);          // V column-major (n x c)
+      if (s) return s;
+    } else {
+      // from the rotated columns, or from the accumulated rotations when the Jacobi ran on the
+      // other side
+      if ((s = run_jacobi(l, c, acc, X, l))) return s;
       const Z* src = acc ? Wacc : X;
       const int len = acc ? c : l;
       if ((s = kl(column_norms<R>(src, len, len, c, norms, stream)))) return s;
@@ -644,6 +720,8 @@ struct Engine final : mps_state {
     out->gates = n_gates;
     out->move_jacobi_launches = n_jac_move;
     out->move_jacobi_ms = jac_move_ms;
+    out->qr_launches = n_qr;
+    out->qr_ms = qr_ms_sum;
     return s;
   }
 
@@ -651,8 +729,8 @@ struct Engine final : mps_state {
     mps_status s;
     if ((s = cu(cudaStreamSynchronize(stream)))) return s;
     harvest();
-    n_launch = n_jac = n_gemm = n_gates = n_jac_move = 0;
-    gemm_flops = jac_ms = gemm_ms = jac_move_ms = 0.0;
+    n_launch = n_jac = n_gemm = n_gates = n_jac_move = n_qr = 0;
+    gemm_flops = jac_ms = gemm_ms = jac_move_ms = qr_ms_sum = 0.0;
     const size_t off = offsetof(DevCtrl, jac_sweeps);
     if ((s = cu(cudaMemsetAsync((char*)ctrl + off, 0, sizeof(DevCtrl) - off, stream)))) return s;
     return cu(cudaStreamSynchronize(stream));

@@ -28,6 +28,13 @@ inline cudaError_t allow_dynamic_smem(const void* fn) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
+// dst(r, j) = op(src[j * ld + r]) for r <= j, 0 below the diagonal (r < rows, j < cols), with
+// dst(r, j) at dst + r * d_rs + j * d_cs and op = conjugation when conj: the triangular factor of
+// a column-major QR result, written in any layout (e.g. its adjoint with d_rs = 1-style strides).
+template <class R>
+cudaError_t triu_extract(cplx<R>* dst, long long d_rs, long long d_cs, const cplx<R>* src, long long ld, int rows,
+                         int cols, int conj, cudaStream_t st);
+
 // Householder QR of the l x c complex64 matrix X (column-major, leading dimension ldx), in place:
 // R in the upper trapezoid, the reflector vectors (unit leading entry implicit) below the
 // diagonal, tau (min(l, c) entries) and the block-reflector factors Tm (32 x 32 per panel of

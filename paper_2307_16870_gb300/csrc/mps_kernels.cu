@@ -479,6 +479,30 @@ cudaError_t chain_contract(int N, const cplx<R>* const* sites, const int* bonds,
 }
 
 template <class R>
+__global__ void triu_extract_kernel(cplx<R>* __restrict__ dst, long long d_rs, long long d_cs,
+                                    const cplx<R>* __restrict__ src, long long ld, int rows, int cols, int conj) {
+  const long long total = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / rows), r = (int)(e % rows);
+    cplx<R> v = mk<R>(0, 0);
+    if (r <= j) {
+      v = src[(long long)j * ld + r];
+      if (conj) v.y = -v.y;
+    }
+    dst[(long long)r * d_rs + (long long)j * d_cs] = v;
+  }
+}
+
+template <class R>
+cudaError_t triu_extract(cplx<R>* dst, long long d_rs, long long d_cs, const cplx<R>* src, long long ld, int rows,
+                         int cols, int conj, cudaStream_t st) {
+  const long long total = (long long)rows * cols;
+  if (total <= 0) return cudaSuccess;
+  triu_extract_kernel<R><<<grid_for(total, 256), 256, 0, st>>>(dst, d_rs, d_cs, src, ld, rows, cols, conj);
+  return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t product_state(cplx<R>* const* sites, int N, int d, cudaStream_t st) {
   product_state_kernel<R><<<grid_for((long long)N * d, 256), 256, 0, st>>>(sites, N, d);
   return cudaGetLastError();
@@ -514,6 +538,8 @@ cudaError_t to_double(const cplx<R>* src, double2* dst, long long count, cudaStr
   template cudaError_t chain_contract<R>(int, const cplx<R>* const*, const int*, int, const double2*, int,      \
                                          const double2*, double2*, int, double2*, cudaStream_t);               \
   template cudaError_t to_double<R>(const cplx<R>*, double2*, long long, cudaStream_t);                        \
+  template cudaError_t triu_extract<R>(cplx<R>*, long long, long long, const cplx<R>*, long long, int, int, int, \
+                                      cudaStream_t);                                                          \
   template cudaError_t product_state<R>(cplx<R>* const*, int, int, cudaStream_t);                            \
   template cudaError_t from_double<R>(const double2*, cplx<R>*, long long, cudaStream_t);
 

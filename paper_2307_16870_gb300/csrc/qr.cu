@@ -28,6 +28,7 @@ constexpr int kQrThreads = 512;
 constexpr int kQrPanel = 32;
 constexpr int kQrTile = 16;
 constexpr int kQrMaxRows = 512;
+constexpr int kQrPanelLd = kQrMaxRows + 1;   // padded column stride of the factored panel
 
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 // conj(a) * b
@@ -36,53 +37,48 @@ __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
 
-__device__ __forceinline__ float2 warp_sum2(float2 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
-
-// Sum of v over the CTA (every thread gets it).  red: 17 floats of shared memory.
-__device__ __forceinline__ float cta_sum(float v, float* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    float s = (lane < kQrThreads / 32) ? red[lane] : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[16] = s;
-  }
-  __syncthreads();
-  const float r = red[16];
-  __syncthreads();
-  return r;
-}
-
 struct QrShared {
   float2 T[kQrPanel * kQrPanel];    // triangular factor of the current panel (row-major)
   float2 tau[kQrPanel];
   float2 w[kQrPanel + 1];           // column products / scale of the current reflector
-  float red[17];
+  float red[1];   // beta of the current reflector
 };
 
-// Factor the panel held column-major in pan (column j at pan + j * kQrMaxRows, rows 0..nr-1,
+// Factor the panel held column-major in pan (column j at pan + j * kQrPanelLd, rows 0..nr-1,
 // rows relative to the panel's first row) into jb reflectors; fills sh.tau and sh.T.
-__device__ void factor_panel(float2* pan, int nr, int jb, QrShared& sh) {
+// Per column j one transposed pass gives d_c = sum_{i > j} conj(x_i) A[i][c] for every column
+// c >= j at once (d_j is the squared norm below the diagonal); with v = x / (alpha - beta) the
+// reflector products are w_c = A[j][c] + conj(scale) d_c, so a column costs three barriers.
+// red2: 16 x 32 partial sums.  Loops are unrolled with two accumulators to keep shared-memory
+// loads in flight.
+__device__ void factor_panel(float2* pan, int nr, int jb, QrShared& sh, float2* red2) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int NW = kQrThreads / 32;
   for (int j = 0; j < jb; ++j) {
-    float2* col = pan + j * kQrMaxRows;
-    float part = 0.f;
-    if (t > j && t < nr) { const float2 x = col[t]; part = x.x * x.x + x.y * x.y; }
-    const float xn2 = cta_sum(part, sh.red);
-    if (t == 0) {
-      const float2 alpha = col[j];
+    const float2* xj = pan + j * kQrPanelLd;
+    // partial d_c over this warp's 32 rows (lane = column c)
+    {
+      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+      const int i0 = max(warp * 32, j + 1), i1 = min(nr, warp * 32 + 32);
+      const float2* ac = pan + lane * kQrPanelLd;
+      if (lane >= j && lane < jb) {
+        int i = i0;
+#pragma unroll 4
+        for (; i + 1 < i1; i += 2) {
+          acc0 = c_add(acc0, c_mulc(xj[i], ac[i]));
+          acc1 = c_add(acc1, c_mulc(xj[i + 1], ac[i + 1]));
+        }
+        if (i < i1) acc0 = c_add(acc0, c_mulc(xj[i], ac[i]));
+      }
+      red2[warp * 32 + lane] = c_add(acc0, acc1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float2 dc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) dc = c_add(dc, red2[w * 32 + lane]);
+      const float xn2 = __shfl_sync(0xffffffffu, dc.x, j);
+      const float2 alpha = xj[j];
       float2 tj = make_float2(0.f, 0.f), sc = make_float2(0.f, 0.f);
       float beta = alpha.x;
       if (!(xn2 == 0.f && alpha.y == 0.f)) {
@@ -93,33 +89,31 @@ __device__ void factor_panel(float2* pan, int nr, int jb, QrShared& sh) {
         const float dd = den.x * den.x + den.y * den.y;
         sc = make_float2(den.x / dd, -den.y / dd);
       }
-      sh.tau[j] = tj;
-      sh.w[kQrPanel] = sc;
-      col[j] = make_float2(beta, 0.f);
-    }
-    __syncthreads();
-    const float2 sc = sh.w[kQrPanel];
-    const float2 tj = sh.tau[j];
-    if (t > j && t < nr) col[t] = c_mul(col[t], sc);
-    __syncthreads();
-    // w_c = v_j^dagger A[:, c] over rows j..nr-1 (v_j[j] = 1)
-    for (int cc = j + 1 + warp; cc < jb; cc += NW) {
-      const float2* a = pan + cc * kQrMaxRows;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int i = j + lane; i < nr; i += 32) {
-        const float2 v = (i == j) ? make_float2(1.f, 0.f) : col[i];
-        acc = c_add(acc, c_mulc(v, a[i]));
+      if (lane > j && lane < jb) sh.w[lane] = c_add(pan[lane * kQrPanelLd + j], c_mul(c_conj(sc), dc));
+      if (lane == 0) {
+        sh.tau[j] = tj;
+        sh.w[kQrPanel] = sc;
+        sh.red[0] = beta;
       }
-      acc = warp_sum2(acc);
-      if (lane == 0) sh.w[cc] = acc;
     }
     __syncthreads();
-    // A[:, c] -= conj(tau_j) v_j w_c  (H_j^dagger applied from the left)
+    // v = x * scale below the diagonal, R[j][j] = beta, and A[i][c] -= conj(tau) v_i w_c
     if (t >= j && t < nr) {
-      const float2 v = (t == j) ? make_float2(1.f, 0.f) : col[t];
-      const float2 ctv = c_mul(c_conj(tj), v);
+      const float2 sc = sh.w[kQrPanel];
+      const float2 ctau = c_conj(sh.tau[j]);
+      float2* col = pan + j * kQrPanelLd;
+      float2 v;
+      if (t == j) {
+        v = make_float2(1.f, 0.f);
+        col[j] = make_float2(sh.red[0], 0.f);
+      } else {
+        v = c_mul(col[t], sc);
+        col[t] = v;
+      }
+      const float2 ctv = c_mul(ctau, v);
+#pragma unroll 4
       for (int cc = j + 1; cc < jb; ++cc) {
-        float2* a = pan + cc * kQrMaxRows;
+        float2* a = pan + cc * kQrPanelLd;
         a[t] = c_sub(a[t], c_mul(ctv, sh.w[cc]));
       }
     }
@@ -127,22 +121,37 @@ __device__ void factor_panel(float2* pan, int nr, int jb, QrShared& sh) {
   }
   // T (forward, columnwise): T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^dagger v_j)
   for (int j = 0; j < jb; ++j) {
-    const float2* vj = pan + j * kQrMaxRows;
+    const float2* vj = pan + j * kQrPanelLd;
     for (int p = warp; p < j; p += NW) {
-      const float2* vp = pan + p * kQrMaxRows;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int i = j + lane; i < nr; i += 32) {
-        const float2 v = (i == j) ? make_float2(1.f, 0.f) : vj[i];
-        acc = c_add(acc, c_mulc(vp[i], v));
+      const float2* vp = pan + p * kQrPanelLd;
+      float2 acc0 = (lane == 0) ? c_conj(vp[j]) : make_float2(0.f, 0.f);   // row j: v_j[j] = 1
+      float2 acc1 = make_float2(0.f, 0.f);
+      int i = j + 1 + lane;
+#pragma unroll 4
+      for (; i + 32 < nr; i += 64) {
+        acc0 = c_add(acc0, c_mulc(vp[i], vj[i]));
+        acc1 = c_add(acc1, c_mulc(vp[i + 32], vj[i + 32]));
       }
-      acc = warp_sum2(acc);
+      if (i < nr) acc0 = c_add(acc0, c_mulc(vp[i], vj[i]));
+      float2 acc = c_add(acc0, acc1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
       if (lane == 0) sh.w[p] = acc;
     }
     __syncthreads();
     if (t < j) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int q = t; q < j; ++q) acc = c_add(acc, c_mul(sh.T[t * kQrPanel + q], sh.w[q]));
-      const float2 v = c_mul(sh.tau[j], acc);
+      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+      int q = t;
+#pragma unroll 4
+      for (; q + 1 < j; q += 2) {
+        acc0 = c_add(acc0, c_mul(sh.T[t * kQrPanel + q], sh.w[q]));
+        acc1 = c_add(acc1, c_mul(sh.T[t * kQrPanel + q + 1], sh.w[q + 1]));
+      }
+      if (q < j) acc0 = c_add(acc0, c_mul(sh.T[t * kQrPanel + q], sh.w[q]));
+      const float2 v = c_mul(sh.tau[j], c_add(acc0, acc1));
       sh.T[t * kQrPanel + j] = make_float2(-v.x, -v.y);
     } else if (t == j) {
       sh.T[j * kQrPanel + j] = sh.tau[j];
@@ -150,6 +159,30 @@ __device__ void factor_panel(float2* pan, int nr, int jb, QrShared& sh) {
       sh.T[t * kQrPanel + j] = make_float2(0.f, 0.f);
     }
     __syncthreads();
+  }
+}
+
+// Copy a rows x cols block (column-major) global -> shared with eight loads in flight per thread.
+__device__ __forceinline__ void load2d(float2* dst, int dld, const float2* src, long long sld, int rows, int cols) {
+  const int total = rows * cols;
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * kQrThreads) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kQrThreads;
+      if (e < total) {
+        const int j = e / rows, i = e - j * rows;
+        v[u] = __ldcg(src + (long long)j * sld + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kQrThreads;
+      if (e < total) {
+        const int j = e / rows, i = e - j * rows;
+        dst[j * dld + i] = v[u];
+      }
+    }
   }
 }
 
@@ -168,11 +201,11 @@ __device__ void apply_block(float2* __restrict__ A, long long lda, int nr, int t
                             const float2* Ts, bool adjoint, float2* At, float2* As, float2* W) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int NW = kQrThreads / 32;
-  // stage the tile (one warp per column, coalesced), zero columns past tw
-  for (int c = warp; c < kQrTile; c += NW) {
-    const float2* src = A + (long long)c * lda;
-    float2* dst = At + c * kQrMaxRows;
-    for (int i = lane; i < nr; i += 32) dst[i] = (c < tw) ? __ldcg(src + i) : make_float2(0.f, 0.f);
+  // stage the tile, zero columns past tw
+  load2d(At, kQrMaxRows, A, lda, nr, tw);
+  for (int e = tw * nr + t; e < kQrTile * nr; e += kQrThreads) {
+    const int c = e / nr, i = e - c * nr;
+    At[c * kQrMaxRows + i] = make_float2(0.f, 0.f);
   }
   __syncthreads();
   // W1[p][c] = sum_i conj(V[i][p]) A[i][c]: lane = p; warp -> column quad cq, row slice ks
@@ -236,14 +269,27 @@ __device__ void apply_block(float2* __restrict__ A, long long lda, int nr, int t
 
 // Explicit reflector vectors of the panel at column c0 (rows r0.., column-major in X) into Vs.
 __device__ void load_v(const float2* X, long long ldx, int r0, int nr, int c0, int jb, float2* Vs) {
-  for (int e = threadIdx.x; e < nr * kQrPanel; e += kQrThreads) {
-    const int p = e / nr, i = e % nr;          // coalesced along rows of one column
-    float2 v = make_float2(0.f, 0.f);
-    if (p < jb) {
-      if (i == p) v = make_float2(1.f, 0.f);
-      else if (i > p) v = __ldcg(X + (long long)(c0 + p) * ldx + r0 + i);
+  const int total = nr * kQrPanel;
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * kQrThreads) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kQrThreads;
+      const int p = e / nr, i = e - p * nr;   // coalesced along rows of one column
+      v[u] = make_float2(0.f, 0.f);
+      if (e < total && p < jb) {
+        if (i == p) v[u] = make_float2(1.f, 0.f);
+        else if (i > p) v[u] = __ldcg(X + (long long)(c0 + p) * ldx + r0 + i);
+      }
     }
-    Vs[vsw(i, p)] = v;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * kQrThreads;
+      if (e < total) {
+        const int p = e / nr, i = e - p * nr;
+        Vs[vsw(i, p)] = v[u];
+      }
+    }
   }
 }
 
@@ -258,8 +304,8 @@ struct QrArgs {
 __global__ void __launch_bounds__(kQrThreads, 1) qr_factor_kernel(QrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ QrShared sh;
-  float2* big = reinterpret_cast<float2*>(smem_raw);   // panel (CTA 0) or reflector rows, 512 x 32
-  float2* At = big + kQrMaxRows * kQrPanel;            // staged tile, 16 x 512
+  float2* big = reinterpret_cast<float2*>(smem_raw);   // panel (CTA 0, 32 x 513) or reflector rows (512 x 32)
+  float2* At = big + kQrPanel * kQrPanelLd;            // staged tile, 16 x 512
   float2* As = At + kQrMaxRows * kQrTile;              // 4 x 16 x 32
   float2* W = As + 4 * kQrTile * kQrPanel;             // 16 x 32
   const int P = gridDim.x;
@@ -268,15 +314,12 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_factor_kernel(QrArgs a) {
   for (int k = 0; k < npan; ++k) {
     const int c0 = k * kQrPanel, jb = min(kQrPanel, K - c0), r0 = c0, nr = a.l - r0;
     if (blockIdx.x == 0) {
-      for (int e = threadIdx.x; e < jb * nr; e += kQrThreads) {
-        const int j = e / nr, i = e % nr;
-        big[j * kQrMaxRows + i] = __ldcg(a.X + (long long)(c0 + j) * a.ldx + r0 + i);
-      }
+      load2d(big, kQrPanelLd, a.X + (long long)c0 * a.ldx + r0, a.ldx, nr, jb);
       __syncthreads();
-      factor_panel(big, nr, jb, sh);
+      factor_panel(big, nr, jb, sh, W);
       for (int e = threadIdx.x; e < jb * nr; e += kQrThreads) {
         const int j = e / nr, i = e % nr;
-        __stcg(a.X + (long long)(c0 + j) * a.ldx + r0 + i, big[j * kQrMaxRows + i]);
+        __stcg(a.X + (long long)(c0 + j) * a.ldx + r0 + i, big[j * kQrPanelLd + i]);
       }
       for (int e = threadIdx.x; e < kQrPanel * kQrPanel; e += kQrThreads) a.Tm[(long long)k * kQrPanel * kQrPanel + e] = sh.T[e];
       if (threadIdx.x < jb) a.tau[c0 + threadIdx.x] = sh.tau[threadIdx.x];
@@ -304,7 +347,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_form_q_kernel(QrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ QrShared sh;
   float2* big = reinterpret_cast<float2*>(smem_raw);
-  float2* At = big + kQrMaxRows * kQrPanel;
+  float2* At = big + kQrPanel * kQrPanelLd;
   float2* As = At + kQrMaxRows * kQrTile;
   float2* W = As + 4 * kQrTile * kQrPanel;
   const int P = gridDim.x;
@@ -335,7 +378,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_form_q_kernel(QrArgs a) {
 }
 
 size_t qr_smem_bytes() {
-  return sizeof(float2) * ((size_t)kQrMaxRows * kQrPanel + (size_t)kQrMaxRows * kQrTile + 4 * kQrTile * kQrPanel +
+  return sizeof(float2) * ((size_t)kQrPanel * kQrPanelLd + (size_t)kQrMaxRows * kQrTile + 4 * kQrTile * kQrPanel +
                             kQrTile * kQrPanel);
 }
 

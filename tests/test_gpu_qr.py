@@ -71,3 +71,32 @@ def test_qr_rejects_too_many_rows():
     x = torch.zeros((4, 513), dtype=torch.complex64, device="cuda")
     with pytest.raises(E.MpsError):
         E.mps_qr_c64(513, 4, x.data_ptr(), 513)
+
+
+@pytest.mark.parametrize("mode", ["0", "1", "2"])
+def test_circuit_with_qr_modes_matches_oracle(mode, monkeypatch):
+    """EAMPS_QR = 0 (Jacobi only), 1 (preconditioned gate SVD), 2 (also QR centre moves)."""
+    import workloads as W
+    from oracle import textbook_mps as T
+    from oracle import statevector as SV
+    monkeypatch.setenv("EAMPS_QR", mode)
+    n = 12
+    circ = W.brickwork_circuit(n, 10, 77)
+    m = E.MPS(n, f_min=0.97, n_2q=circ.n_2q, precision=E.TF32X3, log_truncations=False)
+    m.run(circ.gates())
+    o = T.TextbookMPS(n, f_min=0.97, n_2q=circ.n_2q)
+    for q, u in circ.gates():
+        o.apply_2q(q, u)
+    assert m.bond_dims() == o.bond_dims()
+    assert abs(m.fidelity() - o.product) < 1e-4
+    psi = SV.run_circuit(n, circ.gates())
+    got = m.contract()
+    f_true = abs(np.vdot(psi, got)) ** 2 / np.vdot(got, got).real
+    f_orc = abs(np.vdot(psi, o.to_statevector())) ** 2
+    assert abs(f_true - f_orc) < 1e-4
+    st = m.stats()
+    if mode == "0":
+        assert st["qr_launches"] == 0
+    else:
+        assert st["qr_launches"] > 0
+    m.close()
