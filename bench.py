@@ -64,6 +64,9 @@ def parse_args(argv=None):
                          "mpo: the noisy EA-MPO workload (d = 4); "
                          "batch: 64 independent circuits run concurrently; "
                          "strategies: inferred vs true fidelity of the naive/global/nearest schedules")
+    ap.add_argument("--micro-moves", action="store_true",
+                    help="with --micro: shift the gate right by two sites each update, so that every update "
+                         "also moves the orthogonality centre (a QR of a (2 CHI) x CHI site)")
     ap.add_argument("--micro", type=int, default=0, metavar="CHI",
                     help="instead of the circuit: a few two-site updates on a random canonical 24-site MPS "
                          "with every bond CHI (the launch configuration of the circuit's saturated gates)")
@@ -487,17 +490,19 @@ def run_micro(a) -> int:
     import paper_2307_16870_gb300 as E
     prec = {"tf32x3": E.TF32X3, "fp32": E.FP32, "fp64": E.FP64}[a.precision]
     chi, n = a.micro, 24
-    q = n // 2
+    q = n // 2 - (a.steps + 1 if a.micro_moves else 0)
     sites, _ = W.random_canonical_mps(n, chi, q, seed=7)
     m = E.MPS(n, chi_max=chi, fixed_chi=chi, precision=prec, log_truncations=False)
     m.load_sites(sites, q)
     m.profile(True)
     for g in range(max(a.steps, 1) + 1):
-        m.apply_2q(q, W.haar_unitary(4, 3, g), 1.0)
+        pos = q + (2 * g if a.micro_moves else 0)
+        m.apply_2q(min(pos, n - 2), W.haar_unitary(4, 3, g), 1.0)
     torch.cuda.synchronize()
     st = m.stats()
     jl = max(st["jacobi_launches"], 1)
-    print(json.dumps({"micro_chi": chi, "jacobi_ms_per_launch": st["jacobi_ms"] / jl,
+    print(json.dumps({"micro_chi": chi, "moves": bool(a.micro_moves), "qr_launches": st["qr_launches"],
+                      "jacobi_ms_per_launch": st["jacobi_ms"] / jl,
                       "qr_ms_per_launch": st["qr_ms"] / max(st["qr_launches"], 1),
                       "sweeps_per_launch": st["jacobi_sweeps"] / jl,
                       "jacobi_tflops": st["jacobi_flops"] / (st["jacobi_ms"] / 1e3) / 1e12 if st["jacobi_ms"] else None}))

@@ -73,9 +73,9 @@ def test_qr_rejects_too_many_rows():
         E.mps_qr_c64(513, 4, x.data_ptr(), 513)
 
 
-@pytest.mark.parametrize("mode", ["0", "1", "2"])
+@pytest.mark.parametrize("mode", ["0", "1", "2", "3"])
 def test_circuit_with_qr_modes_matches_oracle(mode, monkeypatch):
-    """EAMPS_QR = 0 (Jacobi only), 1 (preconditioned gate SVD), 2 (also QR centre moves)."""
+    """EAMPS_QR bits: 1 the preconditioned gate SVD, 2 the QR centre moves (0: Jacobi only)."""
     import workloads as W
     from oracle import textbook_mps as T
     from oracle import statevector as SV
