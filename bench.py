@@ -297,9 +297,15 @@ def run_ours(a) -> int:
     peak = fp32_peak_tflops(sm_count, 2070.0) if a.precision != "fp64" else None
     jac_s = st["jacobi_ms"] / 1e3
     achieved = (st["jacobi_flops"] / jac_s / 1e12) if jac_s > 0 else None
-    roof = {"bound": "alu", "kernel": "jacobi_kernel (one-sided Jacobi SVD, FP32)",
+    # DRAM bytes of one 512 x 512 launch of the point-to-point kernel (dram__bytes_read.sum +
+    # dram__bytes_write.sum of an ncu capture of the current kernel); the algorithmic bytes of
+    # that launch are one read and one write of theta, 2 x 512 x 512 x 8 B
+    traffic_512 = 2141184 + 31744
+    roof = {"bound": "alu", "kernel": "jacobi_kernel3 and the other one-sided Jacobi SVD kernels, FP32",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "frac": (achieved / peak) if (achieved and peak) else None,
+            "traffic": traffic_512 if a.precision != "fp64" else None,
+            "traffic_launch": "jacobi_kernel3, theta 512 x 512 (bytes per launch; algorithmic 4194304)",
             "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, not measured)",
             "share_of_step": (st["jacobi_ms"] / sum(step_ms)) if step_ms else None,
             "launches": st["jacobi_launches"], "avg_launch_ms": st["jacobi_ms"] / max(st["jacobi_launches"], 1),
