@@ -632,6 +632,7 @@ struct Engine final : mps_state {
     const long long pld = u_type ? n : m;
     const int plen = u_type ? n : m;
     // (a3) selection and FP64 bookkeeping
+    ++n_launch;   // select_bond launches two kernels (FP64 norms, then the selection)
     if ((s = kl(select_bond<R>(tmp2, pld, plen, c, ctrl, target, s_sorted, perm, stream)))) return s;
     if ((s = read_ctrl())) return s;
     const int k = hctrl->k;
@@ -686,6 +687,9 @@ struct Engine final : mps_state {
     centre = 0;
     log.clear();
     sticky = 0;
+    // statistics survive a state reset: take the device's current counters
+    if ((s = cu(cudaMemcpyAsync(hctrl, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, stream)))) return s;
+    if ((s = cu(cudaStreamSynchronize(stream)))) return s;
     const double jf = hctrl->jac_flops;
     const unsigned long long js = hctrl->jac_sweeps;
     std::memset(hctrl, 0, sizeof(DevCtrl));
@@ -698,7 +702,7 @@ struct Engine final : mps_state {
     hctrl->chi_max = chi_cap;
     hctrl->mixed_fid = opt.mixed_fid;
     hctrl->kind = opt.kind;
-    hctrl->jac_flops = jf;   // statistics survive a state reset
+    hctrl->jac_flops = jf;
     hctrl->jac_sweeps = js;
     if ((s = cu(cudaMemcpyAsync(ctrl, hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, stream)))) return s;
     return cu(cudaStreamSynchronize(stream));
@@ -735,6 +739,9 @@ struct Engine final : mps_state {
     gemm_flops = jac_ms = gemm_ms = jac_move_ms = qr_ms_sum = 0.0;
     const size_t off = offsetof(DevCtrl, jac_sweeps);
     if ((s = cu(cudaMemsetAsync((char*)ctrl + off, 0, sizeof(DevCtrl) - off, stream)))) return s;
+    // the host copy too: reset() carries the statistics over from it
+    hctrl->jac_sweeps = 0;
+    hctrl->jac_flops = 0.0;
     return cu(cudaStreamSynchronize(stream));
   }
 

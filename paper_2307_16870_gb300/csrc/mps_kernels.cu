@@ -58,8 +58,7 @@ __device__ __forceinline__ bool before_key(double ka, int ia, double kb, int ib)
 
 // Single CTA of 1024 threads.  Shared: key[n2], idx[n2], cum[n2] (n2 = power of two >= c).
 template <class R>
-__global__ void __launch_bounds__(1024) select_kernel(const cplx<R>* __restrict__ Y, long long ldy, int l, int c,
-                                                      int n2, DevCtrl* ctrl, double target,
+__global__ void __launch_bounds__(1024) select_kernel(int c, int n2, DevCtrl* ctrl, double target,
                                                       double* __restrict__ s_sorted, int* __restrict__ perm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* key = reinterpret_cast<double*>(smem_raw);
@@ -68,16 +67,11 @@ __global__ void __launch_bounds__(1024) select_kernel(const cplx<R>* __restrict_
   __shared__ double part[1024];
   __shared__ int kcount;
   __shared__ double thr_s;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // 1. squared column norms in FP64
-  for (int j = warp; j < n2; j += 32) {
-    double s = 0.0;
-    if (j < c) {
-      const cplx<R>* col = Y + (long long)j * ldy;
-      for (int i = lane; i < l; i += 32) { cplx<R> v = col[i]; s += (double)v.x * v.x + (double)v.y * v.y; }
-      s = warp_sum(s);
-    }
-    if (lane == 0) { key[j] = (j < c) ? s : -1.0; idx[j] = j; }
+  const int tid = threadIdx.x;
+  // 1. squared column norms (FP64, computed across the GPU into s_sorted by colnorm_kernel)
+  for (int j = tid; j < n2; j += blockDim.x) {
+    key[j] = (j < c) ? s_sorted[j] : -1.0;
+    idx[j] = j;
   }
   __syncthreads();
   // 2. bitonic sort, decreasing key, ties by increasing index
@@ -169,7 +163,8 @@ __global__ void __launch_bounds__(1024) select_kernel(const cplx<R>* __restrict_
 }
 
 template <class R>
-__global__ void colnorm_kernel(const cplx<R>* __restrict__ Y, long long ldy, int l, int c, double* __restrict__ out) {
+__global__ void colnorm_kernel(const cplx<R>* __restrict__ Y, long long ldy, int l, int c, double* __restrict__ out,
+                               int squared) {
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= c) return;
@@ -177,7 +172,7 @@ __global__ void colnorm_kernel(const cplx<R>* __restrict__ Y, long long ldy, int
   double s = 0.0;
   for (int i = lane; i < l; i += 32) { cplx<R> v = col[i]; s += (double)v.x * v.x + (double)v.y * v.y; }
   s = warp_sum(s);
-  if (lane == 0) out[j] = sqrt(s);
+  if (lane == 0) out[j] = squared ? s : sqrt(s);
 }
 
 template <class R>
@@ -421,13 +416,18 @@ cudaError_t select_bond(const cplx<R>* Y, long long ldy, int l, int c, DevCtrl* 
   size_t smem = (size_t)n2 * (2 * sizeof(double) + sizeof(int));
   cudaError_t e = allow_dynamic_smem((const void*)select_kernel<R>);
   if (e != cudaSuccess) return e;
-  select_kernel<R><<<1, 1024, smem, st>>>(Y, ldy, l, c, n2, ctrl, target, s_sorted, perm);
+  // squared norms in FP64, one warp per column across (c + 7) / 8 CTAs, into s_sorted; the
+  // selection reads them into shared memory before it writes the sorted values there
+  colnorm_kernel<R><<<(c + 7) / 8, 256, 0, st>>>(Y, ldy, l, c, s_sorted, 1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  select_kernel<R><<<1, 1024, smem, st>>>(c, n2, ctrl, target, s_sorted, perm);
   return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t column_norms(const cplx<R>* Y, long long ldy, int l, int c, double* norms, cudaStream_t st) {
-  colnorm_kernel<R><<<(c + 7) / 8, 256, 0, st>>>(Y, ldy, l, c, norms);
+  colnorm_kernel<R><<<(c + 7) / 8, 256, 0, st>>>(Y, ldy, l, c, norms, 0);
   return cudaGetLastError();
 }
 

@@ -24,3 +24,24 @@ def test_handle_on_a_busy_nonblocking_stream_starts_from_the_product_state():
     # <0..0|U|0..0> on qubits (2, 3): the (0, 0) entry of the gate
     assert abs(m.amplitude([0] * 6) - u[0, 0]) < 1e-5
     m.close()
+
+
+def test_statistics_after_stats_reset_and_state_reset():
+    """Counters zeroed by stats_reset stay zeroed through a later state reset (the benchmark's
+    warm-up runs must not leak into the timed statistics)."""
+    circ = W.brickwork_circuit(10, 8, 3)
+    m = E.MPS(10, f_min=0.99, n_2q=circ.n_2q, log_truncations=False)
+    m.run(circ.gates())
+    m.stats_reset()
+    m.reset()
+    st = m.stats()
+    assert st["jacobi_sweeps"] == 0 and st["jacobi_flops"] == 0.0 and st["jacobi_launches"] == 0
+    m.run(circ.gates())
+    one = m.stats()
+    m.reset()
+    m.run(circ.gates())
+    two = m.stats()
+    assert one["jacobi_launches"] > 0
+    assert two["jacobi_sweeps"] == 2 * one["jacobi_sweeps"]
+    assert two["jacobi_flops"] == pytest.approx(2 * one["jacobi_flops"], rel=1e-12)
+    m.close()
