@@ -59,11 +59,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
-    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies"],
+    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies", "grad"],
                     help="ttf: time to target fidelity, EA against fixed bond dimensions; "
                          "mpo: the noisy EA-MPO workload (d = 4); "
                          "batch: 64 independent circuits run concurrently; "
-                         "strategies: inferred vs true fidelity of the naive/global/nearest schedules")
+                         "strategies: inferred vs true fidelity of the naive/global/nearest schedules; "
+                         "grad: parameter-shift gradients of the layered ansatz as one batch")
     ap.add_argument("--micro-moves", action="store_true",
                     help="with --micro: shift the gate right by two sites each update, so that every update "
                          "also moves the orthogonality centre (a QR of a (2 CHI) x CHI site)")
@@ -373,7 +374,9 @@ def run_study(a) -> int:
     {0.9, 0.99}, bond cap 128) through mps_batch_run at concurrency 1, 4, 8, 16;
     wall time of the whole batch (host threads included).  strategies: an 18-qubit
     depth-18 brickwork at F_min 0.9 and 0.5 under each schedule; the true
-    fidelity |<exact|EA>|^2 comes from mps_overlap with the untruncated run.
+    fidelity |<exact|EA>|^2 comes from mps_overlap with the untruncated run.  grad: the
+    parameter-shift gradient (2P + 1 circuits) of sum_i <Z_i Z_{i+1}> for the layered ansatz,
+    20 qubits x 3 layers untruncated and 40 qubits x 2 layers at F_min 0.99, as one batch.
     """
     import torch
     import paper_2307_16870_gb300 as E
@@ -457,6 +460,23 @@ def run_study(a) -> int:
                       "exact_max_bond": max(exact.bond_dims())})
                 m.close()
         exact.close()
+    elif a.study == "grad":
+        from paper_2307_16870_gb300 import grad as G
+        for n_q, layers, f_min, cap in ((20, 3, 1.0, 0), (40, 2, 0.99, 64)):
+            p = W.ansatz_params(n_q, layers, a.seed)
+            fn = (lambda nq, ly: (lambda ang: W.ansatz_circuit(nq, ly, ang)))(n_q, layers)
+            G.energy_and_grad(fn, n_q, p, f_min=f_min, chi_max=cap, concurrency=8, with_grad=False)   # warm-up
+            for conc in (1, 8):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                e, g, info = G.energy_and_grad(fn, n_q, p, f_min=f_min, chi_max=cap, concurrency=conc)
+                torch.cuda.synchronize(dev)
+                dt = time.perf_counter() - t0
+                emit({"study": "grad", "n_qubits": n_q, "layers": layers, "params": int(p.size), "f_min": f_min,
+                      "chi_cap": cap, "concurrency": conc, "circuits": info["circuits"], "updates": info["updates"],
+                      "wall_s": dt, "updates_per_s": info["updates"] / dt, "energy": e,
+                      "grad_norm": float(np.linalg.norm(g)),
+                      "min_inferred_fidelity": float(min(info["inferred_fidelity"]))})
     elif a.study == "batch":
         specs = W.random_batch_specs(64, a.seed)
         cap = 128

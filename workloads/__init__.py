@@ -24,6 +24,8 @@ Contents
 * Textbook Kraus operators of the noise models: two-qubit depolarising noise
   and single-qubit amplitude damping.
 * Random circuit batches of uneven size.
+* A layered variational ansatz: per layer RY then RZ on every qubit, then RZZ on
+  the pairs (0,1), (1,2), ..., (n-2,n-1) in that order, with seeded angles.
 
 Index convention for a gate on qubits (q, q+1): a 4x4 matrix acting on the
 basis |s_q s_{q+1}> with s_q the more significant bit.
@@ -48,6 +50,8 @@ __all__ = [
     "random_batch_specs",
     "count_brickwork_gates",
     "random_canonical_mps",
+    "ansatz_params",
+    "ansatz_circuit",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -245,3 +249,45 @@ def random_canonical_mps(n, chi_cap, centre, seed, d=2, round_c64=True):
             t = t.astype(np.complex64).astype(np.complex128)
         sites.append(np.ascontiguousarray(t))
     return sites, bonds
+
+
+def ansatz_params(n_qubits: int, layers: int, seed: int) -> np.ndarray:
+    """Seeded angles U[0, 2 pi) of ansatz_circuit: per layer n RY, n RZ, n-1 RZZ angles."""
+    return 2.0 * math.pi * uniforms(seed, 0, layers * (3 * n_qubits - 1))
+
+
+def _ry(t: float) -> np.ndarray:
+    c, s = math.cos(t / 2), math.sin(t / 2)
+    return np.array([[c, -s], [s, c]], np.complex128)
+
+
+def _rz(t: float) -> np.ndarray:
+    return np.diag([np.exp(-0.5j * t), np.exp(0.5j * t)])
+
+
+def _rzz(t: float) -> np.ndarray:
+    a, b = np.exp(-0.5j * t), np.exp(0.5j * t)
+    return np.diag([a, b, b, a])
+
+
+def ansatz_circuit(n_qubits: int, layers: int, params) -> Circuit:
+    """The layered ansatz as nearest-neighbour two-qubit gates only.
+
+    Layer l applies RY(a) then RZ(b) to every qubit, then RZZ(g) = exp(-i g Z x Z / 2) to
+    (0,1), (1,2), ..., (n-2,n-1) in that order.  Each qubit's single-qubit rotation is folded
+    into the first two-qubit gate that touches it: gate (0,1) = RZZ (R_0 x R_1), gate (i,i+1) =
+    RZZ (1 x R_{i+1}) for i >= 1, with R = RZ(b) RY(a).  Every angle is exp(-i t P / 2) for a
+    Pauli product P, so the parameter-shift rule applies to each.
+    """
+    p = np.asarray(params, dtype=np.float64).reshape(layers, 3 * n_qubits - 1)
+    qs, ops, lay = [], [], []
+    eye = np.eye(2, dtype=np.complex128)
+    for l in range(layers):
+        ry, rz, zz = p[l, :n_qubits], p[l, n_qubits:2 * n_qubits], p[l, 2 * n_qubits:]
+        r = [_rz(rz[i]) @ _ry(ry[i]) for i in range(n_qubits)]
+        for i in range(n_qubits - 1):
+            local = np.kron(r[0], r[1]) if i == 0 else np.kron(eye, r[i + 1])
+            qs.append(i)
+            ops.append(_rzz(zz[i]) @ local)
+            lay.append(l)
+    return Circuit(n_qubits, qs, ops, lay, 0)
