@@ -59,12 +59,13 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
-    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies", "grad"],
+    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies", "grad", "vidal"],
                     help="ttf: time to target fidelity, EA against fixed bond dimensions; "
                          "mpo: the noisy EA-MPO workload (d = 4); "
                          "batch: 64 independent circuits run concurrently; "
                          "strategies: inferred vs true fidelity of the naive/global/nearest schedules; "
-                         "grad: parameter-shift gradients of the layered ansatz as one batch")
+                         "grad: parameter-shift gradients of the layered ansatz as one batch; "
+                         "vidal: the Vidal/Hastings form against the canonical update")
     ap.add_argument("--micro-moves", action="store_true",
                     help="with --micro: shift the gate right by two sites each update, so that every update "
                          "also moves the orthogonality centre (a QR of a (2 CHI) x CHI site)")
@@ -377,6 +378,8 @@ def run_study(a) -> int:
     fidelity |<exact|EA>|^2 comes from mps_overlap with the untruncated run.  grad: the
     parameter-shift gradient (2P + 1 circuits) of sum_i <Z_i Z_{i+1}> for the layered ansatz,
     20 qubits x 3 layers untruncated and 40 qubits x 2 layers at F_min 0.99, as one batch.
+    vidal: inferred against true fidelity of the canonical and the Vidal/Hastings form (18 qubits,
+    depth 18), and their throughput on the 100-qubit depth-30 circuit.
     """
     import torch
     import paper_2307_16870_gb300 as E
@@ -460,6 +463,42 @@ def run_study(a) -> int:
                       "exact_max_bond": max(exact.bond_dims())})
                 m.close()
         exact.close()
+    elif a.study == "vidal":
+        # (1) inferred against true fidelity, canonical and Vidal form, 18 qubits depth 18
+        n_q, depth = 18, 18
+        circ = W.brickwork_circuit(n_q, depth, a.seed)
+        n = circ.n_2q
+        ops_dev = torch.from_numpy(circ.ops_array().view(np.float64).reshape(n, 32).copy()).to(dev)
+        qs = np.asarray(circ.qs, dtype=np.int32)
+        exact = E.MPS(n_q, n_2q=n, precision=prec, log_truncations=False)
+        E.mps_apply_circuit_device(exact.h, qs, ops_dev.data_ptr(), 4, 1.0)
+        for f_min in (0.9, 0.5):
+            for vid in (False, True):
+                m = E.MPS(n_q, f_min=f_min, n_2q=n, precision=prec, log_truncations=False, vidal=vid)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                E.mps_apply_circuit_device(m.h, qs, ops_dev.data_ptr(), 4)
+                inferred = m.fidelity()
+                dt = time.perf_counter() - t0
+                ov = exact.overlap(m)
+                nrm = m.overlap(m).real
+                emit({"study": "vidal", "n_qubits": n_q, "depth": depth, "f_min": f_min,
+                      "form": "vidal" if vid else "canonical", "inferred_fidelity": inferred,
+                      "true_fidelity": abs(ov) ** 2 / nrm, "norm2": nrm, "wall_s": dt,
+                      "max_bond": max(m.bond_dims())})
+                m.close()
+        exact.close()
+        # (2) throughput on the 100-qubit depth-30 circuit, cap 256
+        circ = W.brickwork_circuit(100, 30, a.seed)
+        n = circ.n_2q
+        ops_dev = torch.from_numpy(circ.ops_array().view(np.float64).reshape(n, 32).copy()).to(dev)
+        qs = np.asarray(circ.qs, dtype=np.int32)
+        for vid in (False, True):
+            ms, fid, mx, jms, jl = _timed_circuit(E, torch, dev, 100, qs, ops_dev, 4, f_min=0.9, n_2q=n,
+                                                  strategy=E.GLOBAL, chi_max=256, precision=prec, vidal=vid)
+            emit({"study": "vidal", "n_qubits": 100, "depth": 30, "f_min": 0.9, "chi_cap": 256,
+                  "form": "vidal" if vid else "canonical", "gpu_s": ms / 1e3, "updates_per_s": n / (ms / 1e3),
+                  "inferred_fidelity": fid, "max_bond": mx, "jacobi_share": jms / ms})
     elif a.study == "grad":
         from paper_2307_16870_gb300 import grad as G
         for n_q, layers, f_min, cap in ((20, 3, 1.0, 0), (40, 2, 0.99, 64)):

@@ -74,6 +74,11 @@ typedef struct {
   int mixed_fid;        /* MPO truncation fidelity: MPS_KEPT_RATIO f = W_k/W (default), MPS_WANG_SQRT f = sqrt(W_k/W) */
   int max_sweeps;       /* Jacobi sweep limit (default 40) */
   int log_truncations;  /* keep a host-side record of every truncation (default 1) */
+  int vidal;            /* 1: Vidal/Hastings form (PURE only): every site right-canonical, a Schmidt vector
+                           lambda kept on every bond, no centre moves; a gate on (q, q+1) is truncated from
+                           the SVD of lambda_{q-1} B_q B_{q+1} ("The matrix product formalism": the
+                           canonical form of Vidal), so the gates of a layer are independent.  The
+                           truncation fidelity is exact only while the form stays canonical.  Default 0. */
 } mps_options;
 
 /* One record per two-qubit gate: bond size kept, truncation fidelity f, the

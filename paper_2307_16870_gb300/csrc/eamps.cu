@@ -112,6 +112,7 @@ struct mps_state {
   virtual mps_status stats_reset() = 0;
   // site i (bonds[i] x d x bonds[i+1], row-major) converted to FP64 into dst, ordered on st
   virtual mps_status site_to_double(int i, double2* dst, cudaStream_t st) = 0;
+  virtual bool is_vidal() const = 0;
   int N = 0;
   int d = 2;
   int centre = 0;
@@ -160,6 +161,10 @@ struct Engine final : mps_state {
   Z* qr_T = nullptr;
   int qr_fit = 0;
   bool qr_on = false;
+  // Vidal / Hastings form: Schmidt vector of every bond (FP64), bond b at lam + b * lam_stride
+  bool vidal = false;
+  double* lam = nullptr;
+  int lam_stride = 0;
   int qr_mode = 2;
   // statistics
   long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0, n_jac_move = 0, n_qr = 0;
@@ -174,7 +179,7 @@ struct Engine final : mps_state {
     if (stream) cudaStreamSynchronize(stream);
     coop_release();
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
-                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T};
+                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T, lam};
     for (void* b : bufs) if (b) cudaFree(b);
     if (hctrl) cudaFreeHost(hctrl);
     if (hout) cudaFreeHost(hout);
@@ -329,6 +334,12 @@ struct Engine final : mps_state {
       tc = tc_create(big);
       if (!tc) return MPS_ERR_OOM;
     }
+    vidal = o.vidal != 0;
+    if (vidal) {
+      for (int b = 0; b <= N; ++b) lam_stride = std::max(lam_stride, cap[b]);
+      if (!dalloc(&lam, (size_t)(N + 1) * lam_stride)) return MPS_ERR_OOM;
+      if (mps_status s = reset_lambda()) return s;
+    }
     if (std::is_same<R, float>::value) {
       // EAMPS_QR bits: 1 the QR-preconditioned gate SVD, 2 the centre moves by QR (default 2:
       // measured, the preconditioning saves about as many Jacobi sweeps as its QR costs)
@@ -415,6 +426,15 @@ struct Engine final : mps_state {
       (void)l; (void)c; (void)Xp; (void)ldx; (void)Q; (void)ldq;
       return MPS_ERR_ARG;
     }
+  }
+
+  // Vidal form of a product state: every bond of dimension 1 with Schmidt value 1
+  mps_status reset_lambda() {
+    std::vector<double> h((size_t)(N + 1) * lam_stride, 0.0);
+    for (int b = 0; b <= N; ++b) h[(size_t)b * lam_stride] = 1.0;
+    if (mps_status s = cu(cudaMemcpyAsync(lam, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, stream)))
+      return s;
+    return cu(cudaStreamSynchronize(stream));
   }
 
   mps_status read_ctrl() {
@@ -576,9 +596,11 @@ struct Engine final : mps_state {
       if (!lift(op, op_dim, 2, g)) return MPS_ERR_ARG;
       if ((s = kl(load_gate_param<R>(g.data(), D2, G, stream)))) return s;
     }
-    // (a0) centre onto the pair: to q when it sits at or left of q (leaves at q+1), else to q+1
-    const bool right = centre <= q;
-    if ((s = move_to(right ? q : q + 1))) return s;
+    // (a0) centre onto the pair: to q when it sits at or left of q (leaves at q+1), else to q+1.
+    // Vidal form: no centre; every update is a leftward one (V^dagger becomes B_{q+1})
+    const bool right = vidal ? false : centre <= q;
+    if (!vidal)
+      if ((s = move_to(right ? q : q + 1))) return s;
     const int cl = bonds[q], chi = bonds[q + 1], cr = bonds[q + 2];
     const int m = d * cl, n = d * cr;
     // (a1) theta = A_q A_{q+1} (m x n as (cl, d, d, cr)), then the gate on the physical pair
@@ -594,6 +616,10 @@ struct Engine final : mps_state {
     const bool cols = use_qr ? !right : (mode == R_COLS || mode == L_COLS_ACC);   // X = theta (else theta^dagger)
     const int l = cols ? m : n, c = cols ? n : m;
     if ((s = kl(gate_theta<R>(T, cl, d, cr, G, X, cols ? 0 : 1, theta, stream)))) return s;
+    // Vidal form: the SVD is of lambda_{q-1} theta (rows of theta scaled by the Schmidt values of
+    // bond q); theta itself stays unscaled for B_q = theta V below
+    if (vidal && q > 0)
+      if ((s = kl(scale_by_lambda<R>(X, l, l, c, lam + (size_t)q * lam_stride, d, cols ? 1 : 0, stream)))) return s;
     // (a2) SVD: one-sided Jacobi gives the singular directions D with unit columns (FP64
     // norms): left vectors U (m x c) for a rightward update, right vectors V (n x c) for a
     // leftward one.  X (l x c, l >= c) is theta or theta^dagger.
@@ -632,8 +658,14 @@ struct Engine final : mps_state {
     const long long pld = u_type ? n : m;
     const int plen = u_type ? n : m;
     // (a3) selection and FP64 bookkeeping
+    const Z* psel = tmp2;
+    if (vidal && q > 0) {   // singular values of lambda_{q-1} theta: the scaled copy of P = theta V
+      if ((s = copy(Wacc, tmp2, (size_t)m * c))) return s;
+      if ((s = kl(scale_by_lambda<R>(Wacc, m, m, c, lam + (size_t)q * lam_stride, d, 1, stream)))) return s;
+      psel = Wacc;
+    }
     ++n_launch;   // select_bond launches two kernels (FP64 norms, then the selection)
-    if ((s = kl(select_bond<R>(tmp2, pld, plen, c, ctrl, target, s_sorted, perm, stream)))) return s;
+    if ((s = kl(select_bond<R>(psel, pld, plen, c, ctrl, target, s_sorted, perm, stream)))) return s;
     if ((s = read_ctrl())) return s;
     const int k = hctrl->k;
     Z* Aq = site[q];
@@ -648,7 +680,11 @@ struct Engine final : mps_state {
       if ((s = extract(Ap, n, 1, k, n, tmp, n, 1, perm, 1, nullptr, 0))) return s;
     }
     bonds[q + 1] = k;
-    centre = right ? q + 1 : q;
+    if (vidal) {
+      if ((s = kl(store_lambda(lam + (size_t)(q + 1) * lam_stride, s_sorted, ctrl, lam_stride, stream)))) return s;
+    } else {
+      centre = right ? q + 1 : q;
+    }
     ++n_gates;
     if (log_on) {
       mps_trunc_record r;
@@ -664,6 +700,8 @@ struct Engine final : mps_state {
     *out = hctrl->product;
     return s;
   }
+
+  bool is_vidal() const override { return vidal; }
 
   mps_status site_to_double(int i, double2* dst, cudaStream_t st) override {
     if (i < 0 || i >= N || !dst) return MPS_ERR_ARG;
@@ -705,7 +743,8 @@ struct Engine final : mps_state {
     hctrl->jac_flops = jf;
     hctrl->jac_sweeps = js;
     if ((s = cu(cudaMemcpyAsync(ctrl, hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, stream)))) return s;
-    return cu(cudaStreamSynchronize(stream));
+    if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+    return vidal ? reset_lambda() : MPS_OK;
   }
 
   mps_status profile(int on) override {
@@ -769,6 +808,7 @@ struct Engine final : mps_state {
 
   mps_status expect(int q, int support, const double* op, double* out) override {
     if (sticky) return from_bits(sticky);
+    if (vidal) return MPS_ERR_STATE;   // the local formula needs a canonical centre on the support
     if (!op || !out || (support != 1 && support != 2) || q < 0 || q + support > N) return MPS_ERR_ARG;
     mps_status s;
     if (d == 2) {
@@ -855,6 +895,7 @@ struct Engine final : mps_state {
 
   mps_status set_site(int i, const double* data, const int* dims3) override {
     if (sticky) return from_bits(sticky);
+    if (vidal) return MPS_ERR_STATE;   // the Schmidt vectors would no longer match the sites
     if (i < 0 || i >= N || !data || !dims3) return MPS_ERR_ARG;
     const int cl = dims3[0], dd = dims3[1], cr = dims3[2];
     if (dd != d || cl < 1 || cr < 1 || cl > cap[i] || cr > cap[i + 1]) return MPS_ERR_ARG;
@@ -908,6 +949,7 @@ void mps_default_options(mps_options* o) {
   o->mixed_fid = MPS_KEPT_RATIO;
   o->max_sweeps = 40;
   o->log_truncations = 1;
+  o->vidal = 0;
 }
 
 const char* mps_status_string(mps_status s) {
@@ -933,7 +975,8 @@ mps_status mps_create(mps_handle* out, int n_qubits, const mps_options* opt, voi
   if (opt->kind != MPS_PURE && opt->kind != MPS_MIXED) return MPS_ERR_ARG;
   if (!(opt->f_min > 0.0) || opt->strategy < 0 || opt->strategy > 2 || opt->chi_max < 0 || opt->fixed_chi < 0 ||
       opt->precision < 0 || opt->precision > 2 || opt->mixed_fid < 0 || opt->mixed_fid > 1 || opt->max_sweeps < 1 ||
-      opt->n_2q < 0 || opt->chi_max > 4096)
+      opt->n_2q < 0 || opt->chi_max > 4096 || opt->vidal < 0 || opt->vidal > 1 ||
+      (opt->vidal && opt->kind != MPS_PURE))
     return MPS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (opt->precision == MPS_FP64) return make_engine<double>(out, n_qubits, *opt, st);
@@ -1162,6 +1205,7 @@ mps_status mps_set_site(mps_handle h, int i, const double* data, const int* dims
 
 mps_status mps_set_centre(mps_handle h, int c) {
   if (!h || c < 0 || c >= h->N) return MPS_ERR_ARG;
+  if (h->is_vidal()) return MPS_ERR_STATE;
   h->centre = c;
   return MPS_OK;
 }

@@ -35,6 +35,14 @@ template <class R>
 cudaError_t triu_extract(cplx<R>* dst, long long d_rs, long long d_cs, const cplx<R>* src, long long ld, int rows,
                          int cols, int conj, cudaStream_t st);
 
+// Vidal / Hastings form: element (r, j) of the column-major Y (leading dimension ld) times
+// lam[r / d] (by_row) or lam[j / d] (columns), lam FP64.
+template <class R>
+cudaError_t scale_by_lambda(cplx<R>* Y, long long ld, int rows, int cols, const double* lam, int d, int by_row,
+                            cudaStream_t st);
+// lam_out[i] = s_sorted[i] / sqrt(ctrl->Wk) for i < ctrl->k (the renormalised kept values).
+cudaError_t store_lambda(double* lam_out, const double* s_sorted, const DevCtrl* ctrl, int cap, cudaStream_t st);
+
 // Householder QR of the l x c complex64 matrix X (column-major, leading dimension ldx), in place:
 // R in the upper trapezoid, the reflector vectors (unit leading entry implicit) below the
 // diagonal, tau (min(l, c) entries) and the block-reflector factors Tm (32 x 32 per panel of

@@ -503,6 +503,40 @@ cudaError_t triu_extract(cplx<R>* dst, long long d_rs, long long d_cs, const cpl
 }
 
 template <class R>
+__global__ void scale_lambda_kernel(cplx<R>* __restrict__ Y, long long ld, int rows, int cols,
+                                    const double* __restrict__ lam, int d, int by_row) {
+  const long long total = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / rows), r = (int)(e % rows);
+    const R f = (R)lam[(by_row ? r : j) / d];
+    cplx<R>& y = Y[(long long)j * ld + r];
+    y.x *= f;
+    y.y *= f;
+  }
+}
+
+template <class R>
+cudaError_t scale_by_lambda(cplx<R>* Y, long long ld, int rows, int cols, const double* lam, int d, int by_row,
+                            cudaStream_t st) {
+  const long long total = (long long)rows * cols;
+  if (total <= 0) return cudaSuccess;
+  scale_lambda_kernel<R><<<grid_for(total, 256), 256, 0, st>>>(Y, ld, rows, cols, lam, d, by_row);
+  return cudaGetLastError();
+}
+
+__global__ void store_lambda_kernel(double* __restrict__ lam_out, const double* __restrict__ s_sorted,
+                                    const DevCtrl* __restrict__ ctrl, int cap) {
+  const int k = min(ctrl->k, cap);
+  const double inv = 1.0 / sqrt(ctrl->Wk);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) lam_out[i] = s_sorted[i] * inv;
+}
+
+cudaError_t store_lambda(double* lam_out, const double* s_sorted, const DevCtrl* ctrl, int cap, cudaStream_t st) {
+  store_lambda_kernel<<<grid_for(cap, 256), 256, 0, st>>>(lam_out, s_sorted, ctrl, cap);
+  return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t product_state(cplx<R>* const* sites, int N, int d, cudaStream_t st) {
   product_state_kernel<R><<<grid_for((long long)N * d, 256), 256, 0, st>>>(sites, N, d);
   return cudaGetLastError();
@@ -538,6 +572,7 @@ cudaError_t to_double(const cplx<R>* src, double2* dst, long long count, cudaStr
   template cudaError_t chain_contract<R>(int, const cplx<R>* const*, const int*, int, const double2*, int,      \
                                          const double2*, double2*, int, double2*, cudaStream_t);               \
   template cudaError_t to_double<R>(const cplx<R>*, double2*, long long, cudaStream_t);                        \
+  template cudaError_t scale_by_lambda<R>(cplx<R>*, long long, int, int, const double*, int, int, cudaStream_t); \
   template cudaError_t triu_extract<R>(cplx<R>*, long long, long long, const cplx<R>*, long long, int, int, int, \
                                       cudaStream_t);                                                          \
   template cudaError_t product_state<R>(cplx<R>* const*, int, int, cudaStream_t);                            \

@@ -1,0 +1,61 @@
+"""Pins of the Vidal / Hastings oracle against definitions: the exact state, the exact Schmidt
+values of every cut, right-canonicality, and the exact single-cut fidelity of a first truncation."""
+import numpy as np
+
+import workloads as W
+from oracle import statevector as SV
+from oracle import textbook_mps as T
+from oracle.vidal import VidalMPS
+
+
+def _schmidt(psi, n, b):
+    s = np.linalg.svd(psi.reshape(2 ** b, 2 ** (n - b)), compute_uv=False)
+    return s[s > 1e-12]
+
+
+def test_untruncated_vidal_is_exact_with_exact_schmidt_vectors():
+    n = 8
+    circ = W.brickwork_circuit(n, 6, 91)
+    v = VidalMPS(n)
+    psi = SV.zero_state(n)
+    for q, u in circ.gates():
+        v.apply_2q(q, u)
+        psi = SV.apply_2q(psi, n, q, u)
+        got = _schmidt(psi, n, q + 1)
+        lam = v.lam[q + 1][v.lam[q + 1] > 1e-12]
+        assert np.allclose(lam, got, atol=1e-12)
+    assert abs(abs(np.vdot(psi, v.to_statevector())) - 1.0) < 1e-12
+    assert v.right_canonical_error() < 1e-12
+    assert v.product == 1.0
+
+
+def test_first_truncation_fidelity_is_the_exact_single_cut_fidelity():
+    n = 8
+    circ = W.brickwork_circuit(n, 4, 92)
+    gates = circ.gates()
+    v = VidalMPS(n)
+    psi = SV.zero_state(n)
+    for q, u in gates[:-1]:
+        v.apply_2q(q, u)
+        psi = SV.apply_2q(psi, n, q, u)
+    q, u = gates[-1]
+    rec = v.apply_2q(q, u, target=0.9)
+    psi = SV.apply_2q(psi, n, q, u)
+    assert rec["k"] < rec["rank_bound"]
+    f_true = abs(np.vdot(psi, v.to_statevector())) ** 2
+    assert abs(rec["f"] - f_true) < 1e-12
+
+
+def test_vidal_and_canonical_agree_before_any_truncation_breaks_the_form():
+    """Up to the first truncation both forms hold the same state and decide the same bonds."""
+    n = 10
+    circ = W.brickwork_circuit(n, 8, 93)
+    v = VidalMPS(n, f_min=0.95, n_2q=circ.n_2q)
+    t = T.TextbookMPS(n, f_min=0.95, n_2q=circ.n_2q)
+    for q, u in circ.gates():
+        rv = v.apply_2q(q, u)
+        rt = t.apply_2q(q, u)
+        assert rv["k"] == rt["k"] and abs(rv["f"] - rt["f"]) < 1e-10
+        if rv["k"] < rv["rank_bound"]:
+            break
+    assert abs(abs(np.vdot(v.to_statevector(), t.to_statevector())) - 1.0) < 1e-10
