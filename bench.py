@@ -379,7 +379,8 @@ def run_study(a) -> int:
     parameter-shift gradient (2P + 1 circuits) of sum_i <Z_i Z_{i+1}> for the layered ansatz,
     20 qubits x 3 layers untruncated and 40 qubits x 2 layers at F_min 0.99, as one batch.
     vidal: inferred against true fidelity of the canonical and the Vidal/Hastings form (18 qubits,
-    depth 18), and their throughput on the 100-qubit depth-30 circuit.
+    depth 18), their throughput on the 100-qubit depth-30 circuit, and the Vidal form run layer
+    by layer with the gates of a layer concurrent (concurrency 1, 4, 8, 16; wall time).
     """
     import torch
     import paper_2307_16870_gb300 as E
@@ -499,6 +500,22 @@ def run_study(a) -> int:
             emit({"study": "vidal", "n_qubits": 100, "depth": 30, "f_min": 0.9, "chi_cap": 256,
                   "form": "vidal" if vid else "canonical", "gpu_s": ms / 1e3, "updates_per_s": n / (ms / 1e3),
                   "inferred_fidelity": fid, "max_bond": mx, "jacobi_share": jms / ms})
+        # (3) the Vidal form layer by layer, the gates of each layer concurrently (one target per
+        # layer); wall time including the host threads
+        bounds = [0] + [g for g in range(1, n) if circ.layers[g] != circ.layers[g - 1]] + [n]
+        for conc in (1, 4, 8, 16):
+            m = E.MPS(100, f_min=0.9, n_2q=n, strategy=E.GLOBAL, chi_max=256, precision=prec,
+                      log_truncations=False, vidal=True)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for a0, a1 in zip(bounds[:-1], bounds[1:]):
+                m.apply_layer(qs[a0:a1], ops_dev.data_ptr() + a0 * 256, concurrency=conc)
+            fid = m.fidelity()
+            dt = time.perf_counter() - t0
+            emit({"study": "vidal", "n_qubits": 100, "depth": 30, "f_min": 0.9, "chi_cap": 256,
+                  "form": "vidal_layers", "concurrency": conc, "wall_s": dt, "updates_per_s": n / dt,
+                  "inferred_fidelity": fid, "max_bond": max(m.bond_dims())})
+            m.close()
     elif a.study == "grad":
         from paper_2307_16870_gb300 import grad as G
         for n_q, layers, f_min, cap in ((20, 3, 1.0, 0), (40, 2, 0.99, 64)):

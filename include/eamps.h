@@ -149,6 +149,27 @@ mps_status mps_apply_2q_device(mps_handle h, int q, const double* op_dev, int op
 mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev,
                                     int op_dim, double target);
 
+/* One layer of two-qubit gates on DISJOINT pairs of a Vidal handle
+ * (mps_options.vidal = 1), run concurrently: gate g acts on (qs[g], qs[g]+1)
+ * (qs: host) with the operator at ops_dev + g*32 (DEVICE doubles, op_dim 4).
+ * In the canonical form of Vidal ("The matrix product formalism") a gate
+ * reads the Schmidt vector of its left bond and writes its own sites and
+ * middle bond only, so the gates of a layer are independent.  Up to
+ * `concurrency` of them run at once, each on a helper with its own scratch
+ * and stream (created on first use, kept with the handle) and the handle's
+ * sites and Schmidt vectors; multi-CTA kernels share the SM count.
+ * Every gate of the layer is truncated against ONE per-truncation target:
+ * `target` when >= 0, else the schedule's value (mps_options.strategy) for the
+ * product of fidelities at the layer's start, so the result does not depend
+ * on `concurrency` or on which helper ran which gate.  Afterwards the product
+ * holds all n_gates fidelities and the truncation records are in gate order.
+ * Errors: MPS_ERR_STATE (not a Vidal handle); MPS_ERR_ARG (n_gates < 0, null
+ * pointers with n_gates > 0, op_dim != 4, concurrency < 1, a pair out of
+ * range or two pairs sharing a qubit; nothing has run then).  A failure inside
+ * a gate leaves the handle in the failed state until mps_reset. */
+mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
+                                  double target, int concurrency);
+
 /* One circuit of a batch (mps_batch_run).  The inputs are read and the
  * outputs written by the call; the item array is owned by the caller. */
 typedef struct {

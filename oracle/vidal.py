@@ -61,6 +61,19 @@ class VidalMPS(TextbookMPS):
         self.log.append(rec)
         return rec
 
+    def apply_layer(self, gates, target: float | None = None) -> list:
+        """Gates [(q, op), ...] on disjoint pairs, all truncated against one target: `target` when
+        given (>= 0), else the schedule's value for the product at the layer's start.  In this form
+        every gate reads only its own sites and the Schmidt vector of its left bond, so the order
+        within the layer does not change the result."""
+        used = set()
+        for q, _ in gates:
+            if q in used or q + 1 in used:
+                raise ValueError("gates of a layer must act on disjoint pairs")
+            used.update((q, q + 1))
+        f_t = self.scheduled_target() if (target is None or target < 0) else min(float(target), 1.0)
+        return [self.apply_2q(q, op, f_t) for q, op in gates]
+
     def right_canonical_error(self) -> float:
         """max_i || sum_{s,b} B_i[:, s, b] B_i[:, s, b]^dagger - I ||_max over all sites."""
         err = 0.0

@@ -113,6 +113,8 @@ struct mps_state {
   // site i (bonds[i] x d x bonds[i+1], row-major) converted to FP64 into dst, ordered on st
   virtual mps_status site_to_double(int i, double2* dst, cudaStream_t st) = 0;
   virtual bool is_vidal() const = 0;
+  virtual mps_status apply_layer(int n, const int* qs, const double* ops_dev, int op_dim, double target,
+                                 int concurrency) = 0;
   int N = 0;
   int d = 2;
   int centre = 0;
@@ -165,6 +167,10 @@ struct Engine final : mps_state {
   bool vidal = false;
   double* lam = nullptr;
   int lam_stride = 0;
+  bool lam_owned = true;
+  // helper handles of a Vidal layer run: own scratch and stream, the sites and Schmidt vectors of
+  // this handle
+  std::vector<Engine*> helpers;
   int qr_mode = 2;
   // statistics
   long long n_launch = 0, n_jac = 0, n_gemm = 0, n_gates = 0, n_jac_move = 0, n_qr = 0;
@@ -176,8 +182,10 @@ struct Engine final : mps_state {
   std::vector<cudaEvent_t> ev_pool;
 
   ~Engine() override {
+    for (Engine* h : helpers) delete h;
     if (stream) cudaStreamSynchronize(stream);
     coop_release();
+    if (!lam_owned) lam = nullptr;
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
                     ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T, lam};
     for (void* b : bufs) if (b) cudaFree(b);
@@ -255,7 +263,8 @@ struct Engine final : mps_state {
     return MPS_ERR_CUDA;
   }
 
-  mps_status init(int n, const mps_options& o, cudaStream_t st) {
+  // share != nullptr: a helper of a Vidal layer run, on the sites and Schmidt vectors of share
+  mps_status init(int n, const mps_options& o, cudaStream_t st, const Engine* share = nullptr) {
     N = n;
     opt = o;
     stream = st;
@@ -289,7 +298,7 @@ struct Engine final : mps_state {
       c_max = std::max<int>(c_max, (int)std::max(m, nn));
     }
     const size_t big = std::max(pair_max, site_max);
-    if (!dalloc(&arena, total) || !dalloc(&T, big) || !dalloc(&X, big) || !dalloc(&theta, big) ||
+    if (!(share || dalloc(&arena, total)) || !dalloc(&T, big) || !dalloc(&X, big) || !dalloc(&theta, big) ||
         !dalloc(&Wacc, big) || !dalloc(&tmp, big) || !dalloc(&tmp2, big) || !dalloc(&G, 256) ||
         !dalloc(&O, 256) || !dalloc(&s_sorted, c_max) || !dalloc(&norms, c_max) || !dalloc(&perm, c_max) ||
         !dalloc(&site_dev, N) || !dalloc(&bonds_dev, N + 1) || !dalloc(&ctrl, 1) ||
@@ -305,14 +314,15 @@ struct Engine final : mps_state {
     if (cudaMallocHost((void**)&hctrl, sizeof(DevCtrl)) != cudaSuccess) return MPS_ERR_OOM;
     if (cudaMallocHost((void**)&hout, sizeof(double2) * 4) != cudaSuccess) return MPS_ERR_OOM;
     site.resize(N);
-    for (int i = 0; i < N; ++i) site[i] = arena + off[i];
-    if (mps_status s = cu(cudaMemsetAsync(arena, 0, sizeof(Z) * total, stream))) return s;
+    for (int i = 0; i < N; ++i) site[i] = share ? share->site[i] : arena + off[i];
+    if (!share)
+      if (mps_status s = cu(cudaMemsetAsync(arena, 0, sizeof(Z) * total, stream))) return s;
     // |0> (PURE) or vec(|0><0|) (MIXED, t = 0): entry [0, 0, 0] = 1 on every site.  Every copy
     // is ordered on the handle's stream behind the memset above (a copy on the legacy default
     // stream is not ordered after work on a non-blocking stream); the final synchronisation
     // keeps the host sources alive until the copies have run.
     std::vector<Z> ones(1, mk<R>(1, 0));
-    for (int i = 0; i < N; ++i)
+    for (int i = 0; i < N && !share; ++i)
       if (mps_status s = cu(cudaMemcpyAsync(site[i], ones.data(), sizeof(Z), cudaMemcpyHostToDevice, stream)))
         return s;
     if (mps_status s = cu(cudaMemcpyAsync(site_dev, site.data(), sizeof(Z*) * N, cudaMemcpyHostToDevice, stream)))
@@ -335,7 +345,11 @@ struct Engine final : mps_state {
       if (!tc) return MPS_ERR_OOM;
     }
     vidal = o.vidal != 0;
-    if (vidal) {
+    if (vidal && share) {
+      lam = share->lam;
+      lam_stride = share->lam_stride;
+      lam_owned = false;
+    } else if (vidal) {
       for (int b = 0; b <= N; ++b) lam_stride = std::max(lam_stride, cap[b]);
       if (!dalloc(&lam, (size_t)(N + 1) * lam_stride)) return MPS_ERR_OOM;
       if (mps_status s = reset_lambda()) return s;
@@ -695,6 +709,103 @@ struct Engine final : mps_state {
     return hctrl->cap_hit ? MPS_WARN_CHI_CAP : MPS_OK;
   }
 
+  // One layer of gates on disjoint pairs in Vidal form, up to `concurrency` at a time on helper
+  // handles (own scratch and stream, this handle's sites and Schmidt vectors).  Every gate of the
+  // layer is truncated against the same per-truncation target: `target` when >= 0, else the
+  // schedule's value for the product at the layer's start.
+  mps_status apply_layer(int n, const int* qs, const double* ops_dev, int op_dim, double target,
+                         int concurrency) override {
+    if (sticky) return from_bits(sticky);
+    if (!vidal) return MPS_ERR_STATE;
+    if (n < 0 || (n > 0 && (!qs || !ops_dev)) || concurrency < 1 || op_dim != 4) return MPS_ERR_ARG;
+    if (n == 0) return MPS_OK;
+    std::vector<char> used(N, 0);
+    for (int i = 0; i < n; ++i) {
+      const int q = qs[i];
+      if (q < 0 || q + 1 >= N || used[q] || used[q + 1]) return MPS_ERR_ARG;
+      used[q] = used[q + 1] = 1;
+    }
+    mps_status s = read_ctrl();   // everything of this handle done; product and gate count current
+    if (s != MPS_OK && s != MPS_WARN_CHI_CAP) return s;
+    double ft = target;
+    if (ft < 0.0) {
+      const double p = hctrl->product;
+      if (opt.f_min >= 1.0 || p < opt.f_min) {
+        ft = 1.0;
+      } else {
+        const long long rem = std::max<long long>(opt.n_2q - (long long)hctrl->n_done, 1);
+        if (opt.strategy == MPS_NAIVE) ft = hctrl->f0;
+        else if (opt.strategy == MPS_GLOBAL) ft = std::pow(opt.f_min / p, 1.0 / (double)rem);
+        else ft = opt.f_min / (p * std::pow(hctrl->f0, (double)(rem - 1)));
+        ft = std::min(ft, 1.0);
+      }
+    }
+    const int nh = std::min(concurrency, n);
+    while ((int)helpers.size() < nh) {
+      cudaStream_t hs = nullptr;
+      if (cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) != cudaSuccess) return MPS_ERR_CUDA;
+      Engine* h = new (std::nothrow) Engine<R>();
+      if (!h) { cudaStreamDestroy(hs); return MPS_ERR_OOM; }
+      mps_options ho = opt;
+      ho.log_truncations = 1;
+      if ((s = h->init(N, ho, hs, this)) != MPS_OK) { delete h; cudaStreamDestroy(hs); return s; }
+      h->owns_stream = true;
+      helpers.push_back(h);
+    }
+    for (int w = 0; w < nh; ++w) {
+      Engine* h = helpers[w];
+      h->bonds = bonds;
+      h->log.clear();
+      h->shared_gpu = nh > 1;
+    }
+    std::vector<mps_status> st(n, MPS_OK);
+    const size_t ostride = (size_t)2 * op_dim * op_dim;
+    auto worker = [&](int w) {
+      cudaSetDevice(device);
+      for (int i = w; i < n; i += nh) st[i] = helpers[w]->apply_2q(qs[i], ops_dev + i * ostride, true, op_dim, ft);
+    };
+    if (nh == 1) {
+      worker(0);
+    } else {
+      std::vector<std::thread> pool;
+      for (int w = 0; w < nh; ++w) pool.emplace_back(worker, w);
+      for (std::thread& t : pool) t.join();
+    }
+    mps_status worst = MPS_OK;
+    for (int i = 0; i < n; ++i) {
+      if (st[i] == MPS_WARN_CHI_CAP) {
+        worst = st[i];
+      } else if (st[i] != MPS_OK) {   // the shared sites may be half-updated: this handle fails too
+        for (int w = 0; w < nh; ++w) sticky |= helpers[w]->sticky;
+        if (!sticky) sticky = ST_BAD_ARG;
+        return st[i];
+      }
+    }
+    for (int w = 0; w < nh; ++w)   // the write-back kernels of every helper have finished
+      if ((s = helpers[w]->read_ctrl())) {
+        sticky |= helpers[w]->sticky ? helpers[w]->sticky : ST_BAD_ARG;
+        return s;
+      }
+    // merge: the bonds the layer changed, the truncation records and the product, in gate order
+    // (the same multiplications as gate after gate, whatever the concurrency)
+    for (int i = 0; i < n; ++i) {
+      Engine* h = helpers[i % nh];
+      const mps_trunc_record& r = h->log[i / nh];
+      bonds[qs[i] + 1] = h->bonds[qs[i] + 1];
+      hctrl->product *= r.f;
+      if (log_on) log.push_back(r);
+    }
+    n_gates += n;
+    hctrl->n_done += n;
+    if ((s = cu(cudaMemcpyAsync(&ctrl->product, &hctrl->product, sizeof(double), cudaMemcpyHostToDevice, stream))))
+      return s;
+    if ((s = cu(cudaMemcpyAsync(&ctrl->n_done, &hctrl->n_done, sizeof(hctrl->n_done), cudaMemcpyHostToDevice,
+                                stream))))
+      return s;
+    if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+    return worst;
+  }
+
   mps_status fidelity(double* out) override {
     mps_status s = read_ctrl();
     *out = hctrl->product;
@@ -719,6 +830,7 @@ struct Engine final : mps_state {
   mps_status reset() override {
     mps_status s;
     if ((s = cu(cudaStreamSynchronize(stream)))) return s;
+    fold_helper_stats();
     harvest();
     if ((s = kl(product_state<R>(site_dev, N, d, stream)))) return s;
     std::fill(bonds.begin(), bonds.end(), 1);
@@ -752,6 +864,34 @@ struct Engine final : mps_state {
     return MPS_OK;
   }
 
+  // the layer runs' helper handles are dropped on a state reset; their counters stay in the
+  // handle's statistics
+  mps_stats_t folded{};
+  void fold_helper_stats() {
+    for (Engine* h : helpers) {
+      mps_stats_t t{};
+      h->stats(&t);
+      add_stats(folded, t);
+      delete h;
+    }
+    helpers.clear();
+  }
+  static void add_stats(mps_stats_t& a, const mps_stats_t& b) {
+    a.kernel_launches += b.kernel_launches;
+    a.jacobi_launches += b.jacobi_launches;
+    a.jacobi_sweeps += b.jacobi_sweeps;
+    a.jacobi_ms += b.jacobi_ms;
+    a.jacobi_flops += b.jacobi_flops;
+    a.gemm_launches += b.gemm_launches;
+    a.gemm_ms += b.gemm_ms;
+    a.gemm_flops += b.gemm_flops;
+    a.move_jacobi_launches += b.move_jacobi_launches;
+    a.move_jacobi_ms += b.move_jacobi_ms;
+    a.qr_launches += b.qr_launches;
+    a.qr_ms += b.qr_ms;
+  }
+
+  // gates run on helper handles count once, as gates of this handle
   mps_status stats(mps_stats_t* out) override {
     mps_status s = read_ctrl();
     out->kernel_launches = n_launch;
@@ -767,6 +907,12 @@ struct Engine final : mps_state {
     out->move_jacobi_ms = jac_move_ms;
     out->qr_launches = n_qr;
     out->qr_ms = qr_ms_sum;
+    add_stats(*out, folded);
+    for (Engine* h : helpers) {
+      mps_stats_t t{};
+      h->stats(&t);
+      add_stats(*out, t);
+    }
     return s;
   }
 
@@ -774,6 +920,9 @@ struct Engine final : mps_state {
     mps_status s;
     if ((s = cu(cudaStreamSynchronize(stream)))) return s;
     harvest();
+    for (Engine* h : helpers)
+      if ((s = h->stats_reset())) return s;
+    folded = mps_stats_t{};
     n_launch = n_jac = n_gemm = n_gates = n_jac_move = n_qr = 0;
     gemm_flops = jac_ms = gemm_ms = jac_move_ms = qr_ms_sum = 0.0;
     const size_t off = offsetof(DevCtrl, jac_sweeps);
@@ -1164,6 +1313,12 @@ mps_status mps_overlap(mps_handle a, mps_handle b, double* out_re_im) {
   out_re_im[0] = r.x * scale;
   out_re_im[1] = r.y * scale;
   return MPS_OK;
+}
+
+mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
+                                  double target, int concurrency) {
+  if (!h) return MPS_ERR_ARG;
+  return h->apply_layer(n_gates, qs, ops_dev, op_dim, target, concurrency);
 }
 
 mps_status mps_fidelity(mps_handle h, double* inferred) {
