@@ -170,6 +170,51 @@ mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, co
 mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
                                   double target, int concurrency);
 
+/* ---- Differentiable two-site update (stateless; the paper differentiates nothing) ----
+ * These three calls run the steps of one two-site update (Eq. svd and the cut
+ * of the "Entanglement-aware" section) on caller-owned DEVICE buffers, so that
+ * an autograd layer can chain them and run their derivatives.  They use the
+ * scratch, stream and precision of handle h: complex64 elements (float2) for
+ * MPS_TF32X3 and MPS_FP32 handles, complex128 (double2) for MPS_FP64 handles.
+ * The handle's state, schedule and statistics other than launch counts are
+ * not touched.  Sizes are limited by the handle's scratch: max(m, n) at most
+ * d * (the largest bond cap) and m * n at most its largest two-site block.
+ * All matrices are row-major unless strides say otherwise. */
+
+/* C (M x N) = op(A) op(B), element (r, t) of A at A + r*a_rs + t*a_cs, op =
+ * conjugation when conjA / conjB; C(r, j) at C + r*c_rs + j*c_cs.  M, N, K >= 1.
+ * Asynchronous on the handle's stream.  Errors: MPS_ERR_ARG. */
+mps_status mps_gemm_device(mps_handle h, int M, int N, int K, const void* A, long long a_rs, long long a_cs, int conjA,
+                           const void* B, long long b_rs, long long b_cs, int conjB, void* C, long long c_rs,
+                           long long c_cs);
+
+/* Full thin SVD A = U diag(S) V^H of A (m x n, ld lda >= n) with c = min(m, n):
+ * U (m x c), S (c doubles, descending), V (n x c); one-sided Jacobi on the
+ * short side with FP64 column norms, as in the gate update.  Then the cut:
+ * k = the smallest count with W_k >= target * W (target >= 1 keeps all c),
+ * at most the number of values above rank_tol * S[0], at most max_k when
+ * max_k > 0, at least 1.  Then the write-back of a rightward update:
+ * Aq = U[:, :k] (m x k) and Ap = U_k^H A / sqrt(W_k) = diag(S_k/sqrt(W_k)) V_k^H
+ * (k x n).  Aq and Ap need room for m*c and c*n elements.  out4 (HOST, 4
+ * doubles) receives {k, W_k/W, W, W_k}.  Synchronises the handle's stream.
+ * Errors: MPS_ERR_ARG (sizes, null pointers, target < 0 or NaN, rank_tol < 0),
+ * MPS_ERR_NONFINITE (W_k = 0 or not finite), MPS_ERR_NOT_CONVERGED,
+ * MPS_ERR_TIMEOUT, MPS_ERR_CUDA. */
+mps_status mps_tsvd_device(mps_handle h, int m, int n, const void* A, long long lda, double target, int max_k,
+                           double rank_tol, void* U, double* S, void* V, void* Aq, void* Ap, double* out4);
+
+/* Reverse-mode derivative of mps_tsvd_device: from the factors it returned (U,
+ * S, V) and the cotangents Aq_bar (m x k) and Ap_bar (k x n) of its outputs
+ * (either may be NULL for zero), A_bar (m x n) = dL/dRe A + i dL/dIm A for a
+ * real loss L.  This is the complex SVD adjoint with the gauge term and the
+ * coupling to the discarded values (the exact derivative of the truncated
+ * outputs when the values are distinct).  The factor 1/(s_j^2 - s_i^2) is
+ * broadened to (s_j^2 - s_i^2)/((s_j^2 - s_i^2)^2 + eps), eps >= 0 (0 = exact).
+ * Kept values must be > 0.  Synchronises the handle's stream.
+ * Errors: MPS_ERR_ARG, MPS_ERR_TIMEOUT, MPS_ERR_CUDA. */
+mps_status mps_tsvd_backward_device(mps_handle h, int m, int n, int k, const void* U, const double* S, const void* V,
+                                    const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar);
+
 /* One circuit of a batch (mps_batch_run).  The inputs are read and the
  * outputs written by the call; the item array is owned by the caller. */
 typedef struct {

@@ -27,7 +27,7 @@ __all__ = [
     "mps_truncation_log", "mps_sync", "mps_superop_from_kraus", "mps_status_string",
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
     "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap", "mps_qr_c64",
-    "mps_apply_layer_device",
+    "mps_apply_layer_device", "mps_gemm_device", "mps_tsvd_device", "mps_tsvd_backward_device",
 ]
 
 PURE, MIXED = 0, 1
@@ -124,6 +124,14 @@ def load(path: str | None = None):
         "mps_batch_run": (C.c_int, [C.POINTER(BatchItem), C.c_int, C.c_int, C.POINTER(H)]),
         "mps_overlap": (C.c_int, [H, H, D]),
         "mps_qr_c64": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p, C.c_longlong, C.c_void_p]),
+        "mps_gemm_device": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int,
+                                      C.c_void_p, C.c_longlong, C.c_longlong, C.c_int, C.c_void_p, C.c_longlong,
+                                      C.c_longlong]),
+        "mps_tsvd_device": (C.c_int, [H, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_double, C.c_int, C.c_double,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.POINTER(C.c_double)]),
+        "mps_tsvd_backward_device": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                               C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +212,33 @@ def mps_apply_layer_device(h: int, qs, ops_dev_ptr: int, op_dim: int = 4, target
     return _check(load().mps_apply_layer_device(C.c_void_p(h), int(q.size), q.ctypes.data_as(C.POINTER(C.c_int)),
                                                 C.c_void_p(ops_dev_ptr), int(op_dim), float(target),
                                                 int(concurrency)), "mps_apply_layer_device")
+
+
+def mps_gemm_device(h: int, M: int, N: int, K: int, a: int, a_rs: int, a_cs: int, conj_a: int, b: int, b_rs: int,
+                    b_cs: int, conj_b: int, c: int, c_rs: int, c_cs: int) -> int:
+    """C = op(A) op(B) on device buffers with the handle's scratch and stream (see include/eamps.h)."""
+    return _check(load().mps_gemm_device(C.c_void_p(h), int(M), int(N), int(K), C.c_void_p(a), int(a_rs), int(a_cs),
+                                         int(conj_a), C.c_void_p(b), int(b_rs), int(b_cs), int(conj_b), C.c_void_p(c),
+                                         int(c_rs), int(c_cs)), "mps_gemm_device")
+
+
+def mps_tsvd_device(h: int, m: int, n: int, a: int, lda: int, target: float, max_k: int, rank_tol: float, u: int,
+                    s: int, v: int, aq: int, ap: int) -> tuple:
+    """Truncated SVD and rightward write-back on device buffers; returns (k, W_k/W, W, W_k)."""
+    out = (C.c_double * 4)()
+    _check(load().mps_tsvd_device(C.c_void_p(h), int(m), int(n), C.c_void_p(a), int(lda), float(target), int(max_k),
+                                  float(rank_tol), C.c_void_p(u), C.c_void_p(s), C.c_void_p(v), C.c_void_p(aq),
+                                  C.c_void_p(ap), out), "mps_tsvd_device")
+    return int(out[0]), out[1], out[2], out[3]
+
+
+def mps_tsvd_backward_device(h: int, m: int, n: int, k: int, u: int, s: int, v: int, aq_bar: int, ap_bar: int,
+                             eps: float, a_bar: int) -> int:
+    """Reverse-mode derivative of mps_tsvd_device's outputs (see include/eamps.h)."""
+    return _check(load().mps_tsvd_backward_device(C.c_void_p(h), int(m), int(n), int(k), C.c_void_p(u), C.c_void_p(s),
+                                                  C.c_void_p(v), C.c_void_p(aq_bar or None),
+                                                  C.c_void_p(ap_bar or None), float(eps), C.c_void_p(a_bar)),
+                  "mps_tsvd_backward_device")
 
 
 def mps_qr_c64(l: int, c: int, x_ptr: int, ldx: int, q_ptr: int = 0, ldq: int = 0, stream: int = 0) -> int:

@@ -115,6 +115,13 @@ struct mps_state {
   virtual bool is_vidal() const = 0;
   virtual mps_status apply_layer(int n, const int* qs, const double* ops_dev, int op_dim, double target,
                                  int concurrency) = 0;
+  virtual mps_status gemm_device(int M, int Nn, int K, const void* A, long long a_rs, long long a_cs, int cA,
+                                 const void* B, long long b_rs, long long b_cs, int cB, void* C, long long c_rs,
+                                 long long c_cs) = 0;
+  virtual mps_status tsvd_device(int m, int n, const void* A, long long lda, double target, int max_k,
+                                 double rank_tol, void* U, double* S, void* V, void* Aq, void* Ap, double* out4) = 0;
+  virtual mps_status tsvd_backward_device(int m, int n, int k, const void* U, const double* S, const void* V,
+                                          const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) = 0;
   int N = 0;
   int d = 2;
   int centre = 0;
@@ -147,6 +154,7 @@ struct Engine final : mps_state {
   double *s_sorted = nullptr, *norms = nullptr;
   int* perm = nullptr;
   int c_max = 0;
+  size_t big_cap = 0;   // elements of each two-site scratch buffer
   int last_c = 0;
   DevCtrl* ctrl = nullptr;
   DevCtrl* hctrl = nullptr;
@@ -298,6 +306,7 @@ struct Engine final : mps_state {
       c_max = std::max<int>(c_max, (int)std::max(m, nn));
     }
     const size_t big = std::max(pair_max, site_max);
+    big_cap = big;
     if (!(share || dalloc(&arena, total)) || !dalloc(&T, big) || !dalloc(&X, big) || !dalloc(&theta, big) ||
         !dalloc(&Wacc, big) || !dalloc(&tmp, big) || !dalloc(&tmp2, big) || !dalloc(&G, 256) ||
         !dalloc(&O, 256) || !dalloc(&s_sorted, c_max) || !dalloc(&norms, c_max) || !dalloc(&perm, c_max) ||
@@ -804,6 +813,112 @@ struct Engine final : mps_state {
       return s;
     if ((s = cu(cudaStreamSynchronize(stream)))) return s;
     return worst;
+  }
+
+  // ---------------------------------------------- differentiable two-site update (stateless)
+  // The handle's scratch and stream serve; its state is not touched.
+
+  mps_status gemm_device(int M, int Nn, int K, const void* A, long long a_rs, long long a_cs, int cA, const void* B,
+                         long long b_rs, long long b_cs, int cB, void* C, long long c_rs, long long c_cs) override {
+    if (sticky) return from_bits(sticky);
+    if (M < 1 || Nn < 1 || K < 1 || !A || !B || !C) return MPS_ERR_ARG;
+    return gemm(M, Nn, K, R(1), (const Z*)A, a_rs, a_cs, cA, (const Z*)B, b_rs, b_cs, cB, (Z*)C, c_rs, c_cs);
+  }
+
+  // Full thin SVD of A (m x n, row-major, ld lda): U (m x c), S (c, FP64, descending), V (n x c),
+  // row-major, c = min(m, n); then the cut and the write-back of a rightward update:
+  // Aq = U_k (m x k), Ap = U_k^H A / sqrt(W_k) (k x n).  out4 (host) = {k, W_k/W, W, W_k}.
+  mps_status tsvd_device(int m, int n, const void* Av, long long lda, double target, int max_k, double rank_tol,
+                         void* Uv, double* S, void* Vv, void* Aqv, void* Apv, double* out4) override {
+    if (sticky) return from_bits(sticky);
+    if (m < 1 || n < 1 || !Av || lda < n || !Uv || !S || !Vv || !Aqv || !Apv || !out4 || !(target >= 0.0) ||
+        !(rank_tol >= 0.0))
+      return MPS_ERR_ARG;
+    if (std::max(m, n) > c_max || (size_t)m * n > big_cap) return MPS_ERR_ARG;
+    const Z* A = (const Z*)Av;
+    Z *U = (Z*)Uv, *V = (Z*)Vv;
+    const bool tall = m >= n;   // X = A (tall) or A^H: l x c column-major, l >= c
+    const int l = tall ? m : n, c = tall ? n : m;
+    mps_status s;
+    if (tall) s = extract(X, l, 1, c, l, A, 1, lda, nullptr, 0, nullptr, 0);
+    else s = extract(X, l, 1, c, l, A, lda, 1, nullptr, 1, nullptr, 0);
+    if (s) return s;
+    if ((s = run_jacobi(l, c, true, X, l))) return s;
+    // Vx: the accumulated rotations with unit columns (c x c, column-major, in tmp)
+    if ((s = kl(column_norms<R>(Wacc, c, c, c, norms, stream)))) return s;
+    if ((s = extract(tmp, c, 1, c, c, Wacc, c, 1, nullptr, 0, norms, 0))) return s;
+    // the other factor from the rotated columns of X, each scaled to unit norm (tmp2): the
+    // Jacobi leaves them orthogonal relative to their own norms, so small values keep
+    // orthonormal vectors (X V recomputed from A would not)
+    if ((s = kl(column_norms<R>(X, l, l, c, norms, stream)))) return s;
+    if ((s = extract(tmp2, l, 1, c, l, X, l, 1, nullptr, 0, norms, 0))) return s;
+    // the values: FP64 norms of P = X Vx (l x c, column-major, in T) from the original A
+    if (tall) s = gemm(l, c, c, R(1), A, lda, 1, 0, tmp, 1, c, 0, T, 1, l);
+    else s = gemm(l, c, c, R(1), A, 1, lda, 1, tmp, 1, c, 0, T, 1, l);
+    if (s) return s;
+    if ((s = kl(column_norms<R>(T, l, l, c, norms, stream)))) return s;
+    if ((s = kl(rank_sort(norms, c, perm, s_sorted, stream)))) return s;
+    // A = X: U = the unit rotated columns, V = Vx;  A = X^H: U = Vx, V = the unit rotated
+    // columns (columns in descending order of the values)
+    if (tall) {
+      if ((s = extract(U, 1, c, c, m, tmp2, l, 1, perm, 0, nullptr, 0))) return s;
+      if ((s = extract(V, 1, c, c, n, tmp, c, 1, perm, 0, nullptr, 0))) return s;
+    } else {
+      if ((s = extract(U, 1, c, c, m, tmp, c, 1, perm, 0, nullptr, 0))) return s;
+      if ((s = extract(V, 1, c, c, n, tmp2, l, 1, perm, 0, nullptr, 0))) return s;
+    }
+    double* od = (double*)outdev;
+    if ((s = kl(select_values(s_sorted, c, target, max_k, rank_tol, od, stream)))) return s;
+    if ((s = cu(cudaMemcpyAsync(S, s_sorted, sizeof(double) * c, cudaMemcpyDeviceToDevice, stream)))) return s;
+    if ((s = cu(cudaMemcpyAsync(hout, od, sizeof(double) * 4, cudaMemcpyDeviceToHost, stream)))) return s;
+    if ((s = read_ctrl())) return s;
+    const double* ho = (const double*)hout;
+    const int k = (int)ho[0];
+    const double Wk = ho[3];
+    if (!(Wk > 0.0) || !std::isfinite(Wk) || k < 1 || k > c) return MPS_ERR_NONFINITE;
+    if ((s = extract((Z*)Aqv, 1, k, k, m, U, 1, c, nullptr, 0, nullptr, 0))) return s;
+    if ((s = gemm(k, n, m, R(1.0 / std::sqrt(Wk)), U, 1, c, 1, A, lda, 1, 0, (Z*)Apv, n, 1))) return s;
+    for (int i = 0; i < 4; ++i) out4[i] = ho[i];
+    return cu(cudaStreamSynchronize(stream));
+  }
+
+  // Reverse-mode derivative of tsvd_device's (Aq, Ap) with respect to A (see tsvd_grad.cu)
+  mps_status tsvd_backward_device(int m, int n, int k, const void* Uv, const double* S, const void* Vv,
+                                  const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) override {
+    if (sticky) return from_bits(sticky);
+    const int c = std::min(m, n);
+    if (m < 1 || n < 1 || k < 1 || k > c || !Uv || !S || !Vv || !A_bar || !(eps >= 0.0)) return MPS_ERR_ARG;
+    if (std::max(m, n) > c_max || (size_t)m * n > big_cap) return MPS_ERR_ARG;
+    const Z *U = (const Z*)Uv, *V = (const Z*)Vv;
+    Z* out = (Z*)A_bar;
+    double* wk = (double*)outdev + 4;
+    mps_status s;
+    // Ubar (tmp, m x c), Vbar (tmp2, n x c), sbar (norms)
+    if ((s = kl(tsvd_cotangents<R>(m, n, c, k, V, S, (const Z*)Aq_bar, (const Z*)Ap_bar, tmp, tmp2, norms, wk,
+                                   stream))))
+      return s;
+    // Ju = U^H Ubar (X), Jv = V^H Vbar (theta), c x c row-major
+    if ((s = gemm(c, c, m, R(1), U, 1, c, 1, tmp, c, 1, 0, X, c, 1))) return s;
+    if ((s = gemm(c, c, n, R(1), V, 1, c, 1, tmp2, c, 1, 0, theta, c, 1))) return s;
+    const bool tall = m >= n;
+    if (tall) {   // complement on the U side: Yu = Ubar S^-1 (tmp), Zu = U^H Yu (T)
+      if ((s = kl(tsvd_scale<R>(tmp, m, c, k, S, stream)))) return s;
+      if ((s = gemm(c, c, m, R(1), U, 1, c, 1, tmp, c, 1, 0, T, c, 1))) return s;
+    } else {      // on the V side: Yv = Vbar S^-1 (tmp2), Zv = V^H Yv (T)
+      if ((s = kl(tsvd_scale<R>(tmp2, n, c, k, S, stream)))) return s;
+      if ((s = gemm(c, c, n, R(1), V, 1, c, 1, tmp2, c, 1, 0, T, c, 1))) return s;
+    }
+    if ((s = kl(tsvd_core<R>(c, X, theta, S, norms, eps, T, tall ? 0 : 1, Wacc, stream)))) return s;
+    if (tall) {   // Abar = (U G + Yu) V^H
+      if ((s = gemm(m, c, c, R(1), U, c, 1, 0, Wacc, c, 1, 0, X, c, 1))) return s;
+      if ((s = kl(cadd_strided<R>(X, c, m, c, tmp, c, 1, 0, stream)))) return s;
+      if ((s = gemm(m, n, c, R(1), X, c, 1, 0, V, 1, c, 1, out, n, 1))) return s;
+    } else {      // Abar = U (G V^H + Yv^H)
+      if ((s = gemm(c, n, c, R(1), Wacc, c, 1, 0, V, 1, c, 1, X, n, 1))) return s;
+      if ((s = kl(cadd_strided<R>(X, n, c, n, tmp2, 1, c, 1, stream)))) return s;
+      if ((s = gemm(m, n, c, R(1), U, c, 1, 0, X, n, 1, 0, out, n, 1))) return s;
+    }
+    return read_ctrl();
   }
 
   mps_status fidelity(double* out) override {
@@ -1319,6 +1434,25 @@ mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, cons
                                   double target, int concurrency) {
   if (!h) return MPS_ERR_ARG;
   return h->apply_layer(n_gates, qs, ops_dev, op_dim, target, concurrency);
+}
+
+mps_status mps_gemm_device(mps_handle h, int M, int N, int K, const void* A, long long a_rs, long long a_cs, int conjA,
+                           const void* B, long long b_rs, long long b_cs, int conjB, void* C, long long c_rs,
+                           long long c_cs) {
+  if (!h) return MPS_ERR_ARG;
+  return h->gemm_device(M, N, K, A, a_rs, a_cs, conjA, B, b_rs, b_cs, conjB, C, c_rs, c_cs);
+}
+
+mps_status mps_tsvd_device(mps_handle h, int m, int n, const void* A, long long lda, double target, int max_k,
+                           double rank_tol, void* U, double* S, void* V, void* Aq, void* Ap, double* out4) {
+  if (!h) return MPS_ERR_ARG;
+  return h->tsvd_device(m, n, A, lda, target, max_k, rank_tol, U, S, V, Aq, Ap, out4);
+}
+
+mps_status mps_tsvd_backward_device(mps_handle h, int m, int n, int k, const void* U, const double* S, const void* V,
+                                    const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) {
+  if (!h) return MPS_ERR_ARG;
+  return h->tsvd_backward_device(m, n, k, U, S, V, Aq_bar, Ap_bar, eps, A_bar);
 }
 
 mps_status mps_fidelity(mps_handle h, double* inferred) {

@@ -153,4 +153,28 @@ cudaError_t from_double(const double2* src, cplx<R>* dst, long long count, cudaS
 template <class R>
 cudaError_t to_double(const cplx<R>* src, double2* dst, long long count, cudaStream_t st);
 
+// ------------------------------------------------ differentiable two-site update (tsvd_grad.cu)
+// Descending order of c values: perm[rank] = i, s_sorted[rank] = s[i] (one CTA, c <= a few 1000).
+cudaError_t rank_sort(const double* s, int c, int* perm, double* s_sorted, cudaStream_t st);
+// Truncation of sorted values: out = {k, W_k/W, W, W_k} (device), k from target, rank_tol, max_k.
+cudaError_t select_values(const double* s_sorted, int c, double target, int max_k, double rank_tol, double* out,
+                          cudaStream_t st);
+// Cotangents of the full factors from those of A_q = U_k and A_p = diag(s_k / sqrt(W_k)) V_k^H:
+// Ubar (m x c), Vbar (n x c), sbar (c), W_k into wk[0]; row-major, zero beyond column k.
+template <class R>
+cudaError_t tsvd_cotangents(int m, int n, int c, int k, const cplx<R>* V, const double* s, const cplx<R>* Aq_bar,
+                            const cplx<R>* Ap_bar, cplx<R>* Ubar, cplx<R>* Vbar, double* sbar, double* wk,
+                            cudaStream_t st);
+// Y (rows x c) column i scaled by 1/s_i for i < k (zero otherwise).
+template <class R>
+cudaError_t tsvd_scale(cplx<R>* Y, int rows, int c, int k, const double* s, cudaStream_t st);
+// Core matrix G (c x c) of the SVD adjoint, minus Zc (or Zc^H when zc_adjoint).
+template <class R>
+cudaError_t tsvd_core(int c, const cplx<R>* Ju, const cplx<R>* Jv, const double* s, const double* sbar, double eps,
+                      const cplx<R>* Zc, int zc_adjoint, cplx<R>* G, cudaStream_t st);
+// dst (rows x cols, ld ldd) += op(src) with src(r, j) at src + r * s_rs + j * s_cs.
+template <class R>
+cudaError_t cadd_strided(cplx<R>* dst, long long ldd, int rows, int cols, const cplx<R>* src, long long s_rs,
+                         long long s_cs, int conj, cudaStream_t st);
+
 }  // namespace eamps
