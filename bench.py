@@ -533,6 +533,34 @@ def run_study(a) -> int:
                       "wall_s": dt, "updates_per_s": info["updates"] / dt, "energy": e,
                       "grad_norm": float(np.linalg.norm(g)),
                       "min_inferred_fidelity": float(min(info["inferred_fidelity"]))})
+            g_ps = g
+            # reverse mode through the same truncated simulation (one forward, one backward)
+            from paper_2307_16870_gb300 import autodiff as AD
+            AD.energy_and_grad_ad(n_q, layers, p, f_min=f_min, chi_max=cap or 256)       # warm-up
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            e, g, info = AD.energy_and_grad_ad(n_q, layers, p, f_min=f_min, chi_max=cap or 256)
+            dt = time.perf_counter() - t0
+            emit({"study": "grad", "method": "reverse_mode", "n_qubits": n_q, "layers": layers,
+                  "params": int(p.size), "f_min": f_min, "chi_cap": cap, "wall_s": dt,
+                  "forward_s": info["forward_s"], "backward_s": info["backward_s"],
+                  "svd_updates": info["updates"], "energy": e, "grad_norm": float(np.linalg.norm(g)),
+                  "max_abs_diff_vs_parameter_shift": float(np.abs(g - g_ps).max()),
+                  "inferred_fidelity": info["fidelity"], "max_bond": info["max_bond"]})
+        # the 40-qubit, 10-layer ansatz at F_min 0.99 by reverse mode only (parameter shift would
+        # take 2 * 1190 + 1 circuits)
+        from paper_2307_16870_gb300 import autodiff as AD
+        n_q, layers, f_min, cap = 40, 10, 0.99, 64
+        p = W.ansatz_params(n_q, layers, a.seed)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e, g, info = AD.energy_and_grad_ad(n_q, layers, p, f_min=f_min, chi_max=cap)
+        dt = time.perf_counter() - t0
+        emit({"study": "grad", "method": "reverse_mode", "n_qubits": n_q, "layers": layers, "params": int(p.size),
+              "f_min": f_min, "chi_cap": cap, "wall_s": dt, "forward_s": info["forward_s"],
+              "backward_s": info["backward_s"], "svd_updates": info["updates"], "energy": e,
+              "grad_norm": float(np.linalg.norm(g)), "inferred_fidelity": info["fidelity"],
+              "max_bond": info["max_bond"]})
     elif a.study == "batch":
         specs = W.random_batch_specs(64, a.seed)
         cap = 128

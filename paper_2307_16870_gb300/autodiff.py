@@ -22,12 +22,12 @@ exists; for the untruncated simulation the values dropped that way are zero up t
 """
 from __future__ import annotations
 
-import math
+import time
 
 import numpy as np
 import torch
 
-from . import FP64, GLOBAL, MPS, TF32X3, mps_gemm_device, mps_tsvd_backward_device, mps_tsvd_device
+from . import FP64, MPS, TF32X3, mps_gemm_device, mps_tsvd_backward_device, mps_tsvd_device
 
 __all__ = ["Workspace", "gemm", "tsvd", "DiffMPS", "ansatz_gates_torch", "energy_and_grad_ad"]
 
@@ -282,12 +282,18 @@ def energy_and_grad_ad(n_qubits: int, layers: int, params, f_min: float = 1.0, c
     gates = ansatz_gates_torch(n_qubits, layers, p)
     m = DiffMPS(n_qubits, f_min=f_min, n_2q=len(gates), chi_max=chi_max, precision=precision, eps=eps, ws=ws)
     try:
+        t0 = time.perf_counter()
         for q, g in gates:
             m.apply_2q(q, g)
         e = m.energy_zz()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         e.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         info = {"fidelity": m.product, "k_log": list(m.k_log), "bond_dims": m.bond_dims(),
-                "max_bond": max(m.bond_dims()), "records": m.records}
+                "max_bond": max(m.bond_dims()), "records": m.records, "forward_s": t1 - t0, "backward_s": t2 - t1,
+                "updates": len(m.k_log)}
         return float(e.detach()), p.grad.detach().cpu().numpy().reshape(np.shape(params)), info
     finally:
         m.close()
