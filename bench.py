@@ -59,13 +59,14 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
-    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies", "grad", "vidal"],
+    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies", "grad", "vidal", "precision"],
                     help="ttf: time to target fidelity, EA against fixed bond dimensions; "
                          "mpo: the noisy EA-MPO workload (d = 4); "
                          "batch: 64 independent circuits run concurrently; "
                          "strategies: inferred vs true fidelity of the naive/global/nearest schedules; "
                          "grad: parameter-shift gradients of the layered ansatz as one batch; "
-                         "vidal: the Vidal/Hastings form against the canonical update")
+                         "vidal: the Vidal/Hastings form against the canonical update; "
+                         "precision: tf32x3 / fp32 runs and the differentiable form against FP64 on the GPU")
     ap.add_argument("--micro-moves", action="store_true",
                     help="with --micro: shift the gate right by two sites each update, so that every update "
                          "also moves the orthogonality centre (a QR of a (2 CHI) x CHI site)")
@@ -516,6 +517,55 @@ def run_study(a) -> int:
                   "form": "vidal_layers", "concurrency": conc, "wall_s": dt, "updates_per_s": n / dt,
                   "inferred_fidelity": fid, "max_bond": max(m.bond_dims())})
             m.close()
+    elif a.study == "precision":
+        # the same circuits in complex128 (FP64 throughout) and in the two complex64 modes: the
+        # error of each result against the FP64-on-GPU run
+        def _run(n_q, circ, op_dim, ops_dev, kind, f_min, cap, pr):
+            qs = np.asarray(circ.qs, dtype=np.int32)
+            m = E.MPS(n_q, kind=kind, f_min=f_min, n_2q=circ.n_2q, chi_max=cap, precision=pr)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            E.mps_apply_circuit_device(m.h, qs, ops_dev.data_ptr(), op_dim)
+            fid = m.fidelity()
+            return m, time.perf_counter() - t0, fid
+        names = {E.FP64: "fp64", E.FP32: "fp32", E.TF32X3: "tf32x3"}
+        pure = W.brickwork_circuit(30, 16, a.seed)
+        pure_ops = torch.from_numpy(pure.ops_array().view(np.float64).reshape(pure.n_2q, 32).copy()).to(dev)
+        mpo = W.brickwork_circuit(12, 8, a.seed)
+        ad = E.mps_superop_from_kraus(W.amplitude_damping_kraus(0.005), 1)
+        dep = E.mps_superop_from_kraus(W.depolarizing_2q_kraus(0.01), 2)
+        sops = np.stack([np.kron(ad, ad) @ dep @ E.mps_superop_from_kraus([u], 2) for u in mpo.ops])
+        mpo_ops = torch.from_numpy(np.ascontiguousarray(sops).view(np.float64).reshape(mpo.n_2q, 512).copy()).to(dev)
+        for label, n_q, circ, op_dim, ops_dev, kind, f_min, cap in (
+                ("pure 30q D16", 30, pure, 4, pure_ops, E.PURE, 0.99, 64),
+                ("mpo 12q D8 noisy", 12, mpo, 16, mpo_ops, E.MIXED, 0.95, 64)):
+            ref, t_ref, f_ref = _run(n_q, circ, op_dim, ops_dev, kind, f_min, cap, E.FP64)
+            b_ref = ref.bond_dims()
+            nrm = ref.overlap(ref).real
+            for pr in (E.FP64, E.FP32, E.TF32X3):
+                m, dt, fid = (ref, t_ref, f_ref) if pr == E.FP64 else _run(n_q, circ, op_dim, ops_dev, kind, f_min,
+                                                                           cap, pr)
+                ov = ref.overlap(m)
+                bd = m.bond_dims()
+                emit({"study": "precision", "circuit": label, "precision": names[pr], "f_min": f_min, "chi_cap": cap,
+                      "wall_s": dt, "updates_per_s": circ.n_2q / dt, "inferred_fidelity": fid,
+                      "abs_fidelity_diff_vs_fp64": abs(fid - f_ref),
+                      "overlap_vs_fp64": float(abs(ov) ** 2 / (nrm * m.overlap(m).real)),
+                      "bonds_equal_fp64": int(sum(x == y for x, y in zip(bd, b_ref))), "bonds": len(bd)})
+                if m is not ref:
+                    m.close()
+            ref.close()
+        # the differentiable form: complex64 reverse mode against the FP64 one
+        from paper_2307_16870_gb300 import autodiff as AD
+        for n_q, layers, f_min in ((20, 3, 1.0), (20, 3, 0.95)):
+            p = W.ansatz_params(n_q, layers, a.seed)
+            e64, g64, _ = AD.energy_and_grad_ad(n_q, layers, p, f_min=f_min, chi_max=64, precision=E.FP64)
+            for pr in (E.TF32X3, E.FP32):
+                e, g, info = AD.energy_and_grad_ad(n_q, layers, p, f_min=f_min, chi_max=64, precision=pr)
+                emit({"study": "precision", "circuit": "reverse mode, ansatz %dq x %d layers" % (n_q, layers),
+                      "precision": names[pr], "f_min": f_min, "energy_diff_vs_fp64": abs(e - e64),
+                      "grad_max_abs_diff_vs_fp64": float(np.abs(g - g64).max()),
+                      "grad_norm": float(np.linalg.norm(g64))})
     elif a.study == "grad":
         from paper_2307_16870_gb300 import grad as G
         for n_q, layers, f_min, cap in ((20, 3, 1.0, 0), (40, 2, 0.99, 64)):
@@ -552,15 +602,20 @@ def run_study(a) -> int:
         from paper_2307_16870_gb300 import autodiff as AD
         n_q, layers, f_min, cap = 40, 10, 0.99, 64
         p = W.ansatz_params(n_q, layers, a.seed)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        e, g, info = AD.energy_and_grad_ad(n_q, layers, p, f_min=f_min, chi_max=cap)
-        dt = time.perf_counter() - t0
-        emit({"study": "grad", "method": "reverse_mode", "n_qubits": n_q, "layers": layers, "params": int(p.size),
-              "f_min": f_min, "chi_cap": cap, "wall_s": dt, "forward_s": info["forward_s"],
-              "backward_s": info["backward_s"], "svd_updates": info["updates"], "energy": e,
-              "grad_norm": float(np.linalg.norm(g)), "inferred_fidelity": info["fidelity"],
-              "max_bond": info["max_bond"]})
+        for ckpt in (False, True):
+            torch.cuda.synchronize(dev)
+            torch.cuda.reset_peak_memory_stats(dev)
+            base = torch.cuda.memory_allocated(dev)
+            t0 = time.perf_counter()
+            e, g, info = AD.energy_and_grad_ad(n_q, layers, p, f_min=f_min, chi_max=cap, checkpoint=ckpt)
+            dt = time.perf_counter() - t0
+            emit({"study": "grad", "method": "reverse_mode", "checkpoint_per_layer": ckpt, "n_qubits": n_q,
+                  "layers": layers, "params": int(p.size), "f_min": f_min, "chi_cap": cap, "wall_s": dt,
+                  "forward_s": info["forward_s"], "backward_s": info["backward_s"], "svd_updates": info["updates"],
+                  "svd_calls_with_recompute": info["tsvd_calls"], "energy": e,
+                  "grad_norm": float(np.linalg.norm(g)), "inferred_fidelity": info["fidelity"],
+                  "max_bond": info["max_bond"],
+                  "peak_tensor_bytes": int(torch.cuda.max_memory_allocated(dev) - base)})
     elif a.study == "batch":
         specs = W.random_batch_specs(64, a.seed)
         cap = 128

@@ -155,14 +155,27 @@ class DiffMPS:
         self.n_done = 0
         self.k_log = []
         self.records = []
+        self.tsvd_calls = 0
+        self._replay = None      # iterator over recorded k while a checkpointed layer is recomputed
+        self._layer_ks = None    # k of every update of the layer being run for the first time
 
     def close(self):
         if self.own_ws:
             self.ws.close()
 
     def _tsvd(self, a2, target):
+        self.tsvd_calls += 1
+        if self._replay is not None:
+            # recomputation of a checkpointed layer: the k of the first run, no new decision
+            k = next(self._replay)
+            aq, ap, info = tsvd(self.ws, a2, 1.0, k, 0.0, self.eps)
+            if info["k"] != k:
+                raise RuntimeError("recomputed update kept %d values, the first run %d" % (info["k"], k))
+            return aq, ap, info
         aq, ap, info = tsvd(self.ws, a2, target, self.chi_max, self.rank_tol, self.eps)
         self.k_log.append(info["k"])
+        if self._layer_ks is not None:
+            self._layer_ks.append(info["k"])
         return aq, ap, info
 
     def target(self) -> float:
@@ -208,17 +221,58 @@ class DiffMPS:
         theta = gemm(self.ws, a.reshape(cl * 2, -1), b.reshape(b.shape[0], -1))          # (cl 2) x (2 cr)
         x = theta.reshape(cl, 4, cr).permute(1, 0, 2).reshape(4, cl * cr)
         y = gemm(self.ws, g, x).reshape(4, cl, cr).permute(1, 0, 2).reshape(cl * 2, 2 * cr)
-        f_t = self.target()
+        replay = self._replay is not None
+        f_t = 1.0 if replay else self.target()
         aq, ap, info = self._tsvd(y, f_t)
         k = info["k"]
         self.sites[q] = aq.reshape(cl, 2, k)
         self.sites[q + 1] = ap.reshape(k, 2, cr)
         self.centre = q + 1
-        self.product *= info["f"]
-        self.n_done += 1
         rec = dict(info, q=q, f_t=f_t)
-        self.records.append(rec)
+        if not replay:
+            self.product *= info["f"]
+            self.n_done += 1
+            self.records.append(rec)
         return rec
+
+    def run_layer(self, gates, checkpoint: bool = False):
+        """Apply [(q, g), ...].  With checkpoint, only the layer's input sites are kept for the
+        backward; the layer (centre moves, theta, gates, SVDs) is recomputed when the backward
+        reaches it, with every k as in the first run."""
+        if not checkpoint:
+            for q, g in gates:
+                self.apply_2q(q, g)
+            return
+        from torch.utils.checkpoint import checkpoint as _checkpoint
+        n = self.n
+        qs = [q for q, _ in gates]
+        centre0 = self.centre
+        ks = []
+        first = [True]
+
+        def layer(*tensors):
+            live = (self.sites, self.centre)
+            replay = not first[0]
+            self.sites, self.centre = list(tensors[:n]), centre0
+            if replay:
+                self._replay = iter(ks)
+            else:
+                self._layer_ks = ks
+            try:
+                for q, g in zip(qs, tensors[n:]):
+                    self.apply_2q(q, g)
+                out = tuple(self.sites)
+            finally:
+                # a recomputation may also be cut short by the checkpoint machinery (it stops once
+                # every tensor it needs exists): the live state comes back in every case
+                self._replay = None
+                self._layer_ks = None
+                if replay:
+                    self.sites, self.centre = live
+            first[0] = False
+            return out
+
+        self.sites = list(_checkpoint(layer, *self.sites, *[g for _, g in gates], use_reentrant=False))
 
     def energy_zz(self) -> torch.Tensor:
         """sum_i <Z_i Z_{i+1}> (differentiable), the centre sweeping from site 0."""
@@ -274,17 +328,19 @@ def ansatz_gates_torch(n_qubits: int, layers: int, params: torch.Tensor):
 
 
 def energy_and_grad_ad(n_qubits: int, layers: int, params, f_min: float = 1.0, chi_max: int = 256,
-                       precision: int = TF32X3, eps: float = 0.0, ws: Workspace = None):
+                       precision: int = TF32X3, eps: float = 0.0, ws: Workspace = None, checkpoint: bool = False):
     """Energy sum_i <Z_i Z_{i+1}> of the ansatz state and its gradient by reverse mode through the
-    truncated simulation.  Returns (energy, grad (numpy, shape of params), DiffMPS info dict)."""
+    truncated simulation (checkpoint: per layer, recomputed in the backward).  Returns (energy,
+    grad (numpy, shape of params), info dict)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     p = torch.as_tensor(np.asarray(params, dtype=np.float64), device=dev).clone().requires_grad_(True)
     gates = ansatz_gates_torch(n_qubits, layers, p)
     m = DiffMPS(n_qubits, f_min=f_min, n_2q=len(gates), chi_max=chi_max, precision=precision, eps=eps, ws=ws)
     try:
         t0 = time.perf_counter()
-        for q, g in gates:
-            m.apply_2q(q, g)
+        per = n_qubits - 1
+        for l in range(layers):
+            m.run_layer(gates[l * per:(l + 1) * per], checkpoint)
         e = m.energy_zz()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -293,7 +349,7 @@ def energy_and_grad_ad(n_qubits: int, layers: int, params, f_min: float = 1.0, c
         t2 = time.perf_counter()
         info = {"fidelity": m.product, "k_log": list(m.k_log), "bond_dims": m.bond_dims(),
                 "max_bond": max(m.bond_dims()), "records": m.records, "forward_s": t1 - t0, "backward_s": t2 - t1,
-                "updates": len(m.k_log)}
+                "updates": len(m.k_log), "tsvd_calls": m.tsvd_calls}
         return float(e.detach()), p.grad.detach().cpu().numpy().reshape(np.shape(params)), info
     finally:
         m.close()

@@ -199,3 +199,16 @@ def test_autodiff_gradient_agrees_with_the_batched_parameter_shift():
     e_ps, g_ps, _ = G.energy_and_grad(fn, n, p, concurrency=8)
     assert abs(e_ad - e_ps) < 1e-5
     assert np.abs(g_ad - g_ps).max() < 1e-4
+
+
+def test_per_layer_checkpointing_recomputes_and_gives_the_same_gradient():
+    n, layers, f_min = 10, 3, 0.9
+    p = W.ansatz_params(n, layers, 24)
+    e0, g0, i0 = AD.energy_and_grad_ad(n, layers, p, f_min=f_min, chi_max=64)
+    e1, g1, i1 = AD.energy_and_grad_ad(n, layers, p, f_min=f_min, chi_max=64, checkpoint=True)
+    assert i1["k_log"] == i0["k_log"]
+    assert i1["bond_dims"] == i0["bond_dims"]           # the live state survives the recomputation
+    assert i0["tsvd_calls"] == len(i0["k_log"])
+    assert i1["tsvd_calls"] > len(i1["k_log"])          # the layers ran again in the backward
+    assert abs(e1 - e0) < 1e-12
+    assert np.abs(g1 - g0).max() < 1e-6 * max(1.0, np.abs(g0).max())
