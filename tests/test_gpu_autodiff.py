@@ -212,3 +212,40 @@ def test_per_layer_checkpointing_recomputes_and_gives_the_same_gradient():
     assert i1["tsvd_calls"] > len(i1["k_log"])          # the layers ran again in the backward
     assert abs(e1 - e0) < 1e-12
     assert np.abs(g1 - g0).max() < 1e-6 * max(1.0, np.abs(g0).max())
+
+
+def test_stateless_calls_refuse_bad_arguments(ws32):
+    h = ws32.h
+    a = torch.zeros((8, 8), dtype=torch.complex64, device="cuda")
+    u = torch.zeros((8, 8), dtype=torch.complex64, device="cuda")
+    s = torch.zeros(8, dtype=torch.float64, device="cuda")
+    big = torch.zeros((4096, 4), dtype=torch.complex64, device="cuda")
+    p = a.data_ptr()
+    with pytest.raises(E.MpsError):      # rows beyond the handle's scratch
+        E.mps_tsvd_device(h, 4096, 4, big.data_ptr(), 4, 1.0, 0, 0.0, p, s.data_ptr(), p, p, p)
+    with pytest.raises(E.MpsError):      # negative target
+        E.mps_tsvd_device(h, 8, 8, p, 8, -0.5, 0, 0.0, u.data_ptr(), s.data_ptr(), p, p, p)
+    with pytest.raises(E.MpsError):      # lda < n
+        E.mps_tsvd_device(h, 8, 8, p, 4, 1.0, 0, 0.0, u.data_ptr(), s.data_ptr(), p, p, p)
+    with pytest.raises(E.MpsError):      # k above min(m, n)
+        E.mps_tsvd_backward_device(h, 8, 4, 5, p, s.data_ptr(), p, 0, 0, 0.0, p)
+    with pytest.raises(E.MpsError):      # K = 0
+        E.mps_gemm_device(h, 4, 4, 0, p, 1, 1, 0, p, 1, 1, 0, p, 4, 1)
+    # the handle still works after the refusals
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(_rand(rng, 8, 6)).to(torch.complex64).cuda()
+    aq, ap, info = AD.tsvd(ws32, x, 1.0)
+    assert info["k"] == 6
+
+
+def test_tsvd_of_the_zero_matrix_is_refused():
+    ws = AD.Workspace(8, 16, E.TF32X3)
+    try:
+        a = torch.zeros((8, 8), dtype=torch.complex64, device="cuda")
+        u = torch.zeros((8, 8), dtype=torch.complex64, device="cuda")
+        s = torch.zeros(8, dtype=torch.float64, device="cuda")
+        with pytest.raises(E.MpsError):      # W_k = 0: no direction to keep
+            E.mps_tsvd_device(ws.h, 8, 8, a.data_ptr(), 8, 1.0, 0, 0.0, u.data_ptr(), s.data_ptr(), u.data_ptr(),
+                              u.data_ptr(), u.data_ptr())
+    finally:
+        ws.close()
