@@ -146,3 +146,47 @@ def test_chain_energy_gradient_is_the_parameter_shift_gradient():
         h[j] = 1e-5
         fd = (e_chain(p + h) - e_chain(p - h)) / 2e-5
         assert abs(ps - fd) < 1e-7
+
+
+@pytest.mark.parametrize("m,n", [(11, 6), (6, 11)])
+def test_planted_mistakes_in_the_backward_are_caught(m, n):
+    """The finite-difference pin sees each term of the adjoint: flipping the sign of the phase
+    (gauge) term, or dropping the complement term of the non-square side, fails it."""
+    rng = np.random.default_rng(100 + m)
+    a = _rand(rng, m, n)
+    r = tsvd(a, 0.9)
+    k, u, s, v = r["k"], r["U"], r["S"], r["V"]
+    c = min(m, n)
+    m1, m2 = _rand(rng, m, n), _rand(rng, m, m)
+    w1, w2 = rng.random((m, c)), rng.random((c, n))
+    _, aq_bar, ap_bar = _loss_and_cotangents(r, m1, w1, w2, m2)
+    good = tsvd_backward(u, s, v, k, aq_bar, ap_bar)
+    # the two pieces, recomputed here only to plant the mistakes
+    u_bar = np.zeros((m, c), complex)
+    u_bar[:, :k] = aq_bar
+    sig = s[:k] / math.sqrt(float(np.sum(s[:k] ** 2)))
+    v_bar = np.zeros((n, c), complex)
+    v_bar[:, :k] = ap_bar.conj().T * sig[None, :]
+    ju, jv = u.conj().T @ u_bar, v.conj().T @ v_bar
+    gauge = u @ np.diag(1j * (np.imag(np.diag(ju)) - np.imag(np.diag(jv))) / (2 * s)) @ v.conj().T
+    if m > n:
+        yu = u_bar / s[None, :]
+        comp = (yu - u @ (u.conj().T @ yu)) @ v.conj().T
+    else:
+        yv = v_bar / s[None, :]
+        comp = u @ (yv.conj().T - (yv.conj().T @ v) @ v.conj().T)
+    assert np.linalg.norm(gauge) > 1e-3 and np.linalg.norm(comp) > 1e-3
+
+    def loss(x):
+        return _loss_and_cotangents(tsvd(x, 1.0, k, 0.0), m1, w1, w2, m2)[0]
+
+    h = 1e-6
+    e = _rand(rng, m, n)
+    fd = (loss(a + h * e) - loss(a - h * e)) / (2 * h)
+
+    def dl(g):
+        return float(np.real(np.sum(np.conj(g) * e)))
+
+    assert abs(fd - dl(good)) < 1e-6 * max(1.0, abs(fd))
+    for wrong in (good - 2 * gauge, good - comp):
+        assert abs(fd - dl(wrong)) > 1e-4 * max(1.0, abs(fd))
