@@ -170,6 +170,16 @@ mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, co
 mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
                                   double target, int concurrency);
 
+/* Failure-detection self-test: one device thread waits, in the form every
+ * waiting kernel of the library uses (acquire load, back-off, iteration
+ * limit), for a flag that nothing sets.  After `spins` iterations (1 <= spins
+ * <= 2^31; 10^6 take well under a second) it records the timeout in the
+ * handle's status word and returns: no trap, no fault, the context stays
+ * usable.  Returns MPS_ERR_TIMEOUT; the handle then stays in the failed state
+ * until mps_reset, like after any device-side timeout.
+ * Errors: MPS_ERR_ARG (spins out of range), MPS_ERR_CUDA. */
+mps_status mps_selftest_wait(mps_handle h, long long spins);
+
 /* ---- Differentiable two-site update (stateless; the paper differentiates nothing) ----
  * These three calls run the steps of one two-site update (Eq. svd and the cut
  * of the "Entanglement-aware" section) on caller-owned DEVICE buffers, so that

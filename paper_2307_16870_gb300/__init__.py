@@ -28,6 +28,7 @@ __all__ = [
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
     "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap", "mps_qr_c64",
     "mps_apply_layer_device", "mps_gemm_device", "mps_tsvd_device", "mps_tsvd_backward_device",
+    "mps_selftest_wait",
 ]
 
 PURE, MIXED = 0, 1
@@ -132,6 +133,7 @@ def load(path: str | None = None):
                                       C.POINTER(C.c_double)]),
         "mps_tsvd_backward_device": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+        "mps_selftest_wait": (C.c_int, [H, C.c_longlong]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +241,11 @@ def mps_tsvd_backward_device(h: int, m: int, n: int, k: int, u: int, s: int, v: 
                                                   C.c_void_p(v), C.c_void_p(aq_bar or None),
                                                   C.c_void_p(ap_bar or None), float(eps), C.c_void_p(a_bar)),
                   "mps_tsvd_backward_device")
+
+
+def mps_selftest_wait(h: int, spins: int = 1000000) -> int:
+    """Failure-detection self-test: a bounded device wait that runs out (see include/eamps.h)."""
+    return _check(load().mps_selftest_wait(C.c_void_p(h), int(spins)), "mps_selftest_wait")
 
 
 def mps_qr_c64(l: int, c: int, x_ptr: int, ldx: int, q_ptr: int = 0, ldq: int = 0, stream: int = 0) -> int:

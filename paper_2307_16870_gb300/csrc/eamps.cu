@@ -122,6 +122,7 @@ struct mps_state {
                                  double rank_tol, void* U, double* S, void* V, void* Aq, void* Ap, double* out4) = 0;
   virtual mps_status tsvd_backward_device(int m, int n, int k, const void* U, const double* S, const void* V,
                                           const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) = 0;
+  virtual mps_status selftest_wait(long long spins) = 0;
   int N = 0;
   int d = 2;
   int centre = 0;
@@ -921,6 +922,18 @@ struct Engine final : mps_state {
     return read_ctrl();
   }
 
+  // failure detection: a bounded wait on a word that nothing sets (the selection output slot 6,
+  // zeroed here) gives up, and the status word carries the timeout to the host
+  mps_status selftest_wait(long long spins) override {
+    if (sticky) return from_bits(sticky);
+    if (spins < 1 || spins > (1LL << 31)) return MPS_ERR_ARG;
+    unsigned* flag = (unsigned*)((double*)outdev + 6);
+    mps_status s;
+    if ((s = cu(cudaMemsetAsync(flag, 0, sizeof(unsigned), stream)))) return s;
+    if ((s = kl(wait_probe(flag, 1u, spins, ctrl, stream)))) return s;
+    return read_ctrl();
+  }
+
   mps_status fidelity(double* out) override {
     mps_status s = read_ctrl();
     *out = hctrl->product;
@@ -1453,6 +1466,11 @@ mps_status mps_tsvd_backward_device(mps_handle h, int m, int n, int k, const voi
                                     const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) {
   if (!h) return MPS_ERR_ARG;
   return h->tsvd_backward_device(m, n, k, U, S, V, Aq_bar, Ap_bar, eps, A_bar);
+}
+
+mps_status mps_selftest_wait(mps_handle h, long long spins) {
+  if (!h) return MPS_ERR_ARG;
+  return h->selftest_wait(spins);
 }
 
 mps_status mps_fidelity(mps_handle h, double* inferred) {
