@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--fixed-chi", type=int, default=0)
     ap.add_argument("--seed", type=int, default=1002)
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
+    ap.add_argument("--svd-kernel", default="auto", choices=["auto", "tournament", "gram"],
+                    help="layout of the Jacobi SVD (mps_options.svd_kernel)")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0, help="seconds of oracle work per CPU sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -232,7 +234,7 @@ def run_ours(a) -> int:
     qs = np.asarray(circ.qs, dtype=np.int32)
     stream = torch.cuda.current_stream(dev)
     m = E.MPS(a.n_qubits, f_min=a.f_min, n_2q=n, strategy=E.GLOBAL, chi_max=a.chi_cap, fixed_chi=a.fixed_chi,
-              precision=prec, log_truncations=False, stream=stream.cuda_stream)
+              precision=prec, log_truncations=False, stream=stream.cuda_stream, svd_kernel=svd_kernel_of(a, E))
     flush = torch.empty(a.flush_mb * (1 << 20) // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -649,6 +651,10 @@ def run_study(a) -> int:
     return 0
 
 
+def svd_kernel_of(a, E) -> int:
+    return {"auto": E.SVD_AUTO, "tournament": E.SVD_TOURNAMENT, "gram": E.SVD_GRAM}[a.svd_kernel]
+
+
 def run_micro(a) -> int:
     """Per-launch Jacobi timing of saturated updates (used for focused profiling)."""
     import torch
@@ -657,7 +663,7 @@ def run_micro(a) -> int:
     chi, n = a.micro, 24
     q = n // 2 - (a.steps + 1 if a.micro_moves else 0)
     sites, _ = W.random_canonical_mps(n, chi, q, seed=7)
-    m = E.MPS(n, chi_max=chi, fixed_chi=chi, precision=prec, log_truncations=False)
+    m = E.MPS(n, chi_max=chi, fixed_chi=chi, precision=prec, log_truncations=False, svd_kernel=svd_kernel_of(a, E))
     m.load_sites(sites, q)
     m.profile(True)
     for g in range(max(a.steps, 1) + 1):
@@ -666,7 +672,8 @@ def run_micro(a) -> int:
     torch.cuda.synchronize()
     st = m.stats()
     jl = max(st["jacobi_launches"], 1)
-    print(json.dumps({"micro_chi": chi, "moves": bool(a.micro_moves), "qr_launches": st["qr_launches"],
+    print(json.dumps({"micro_chi": chi, "svd_kernel": a.svd_kernel, "moves": bool(a.micro_moves),
+                      "qr_launches": st["qr_launches"],
                       "jacobi_ms_per_launch": st["jacobi_ms"] / jl,
                       "qr_ms_per_launch": st["qr_ms"] / max(st["qr_launches"], 1),
                       "sweeps_per_launch": st["jacobi_sweeps"] / jl,

@@ -61,6 +61,8 @@ enum { MPS_PURE = 0, MPS_MIXED = 1 };                          /* mps_options.ki
 enum { MPS_NAIVE = 0, MPS_GLOBAL = 1, MPS_NEAREST = 2 };       /* mps_options.strategy */
 enum { MPS_FP64 = 0, MPS_TF32X3 = 1, MPS_FP32 = 2 };           /* mps_options.precision */
 enum { MPS_KEPT_RATIO = 0, MPS_WANG_SQRT = 1 };                /* mps_options.mixed_fid */
+enum { MPS_SVD_AUTO = 0, MPS_SVD_TOURNAMENT = 1, MPS_SVD_GRAM = 2 };  /* mps_options.svd_kernel */
+enum { MPS_QR_PRECONDITION = 1, MPS_QR_MOVES = 2 };             /* mps_options.qr (bit flags) */
 
 typedef struct {
   int kind;             /* MPS_PURE (d = 2) or MPS_MIXED (d = 4) */
@@ -79,6 +81,16 @@ typedef struct {
                            the SVD of lambda_{q-1} B_q B_{q+1} ("The matrix product formalism": the
                            canonical form of Vidal), so the gates of a layer are independent.  The
                            truncation fidelity is exact only while the form stays canonical.  Default 0. */
+  int svd_kernel;       /* layout of the one-sided Jacobi SVD (complex64; every layout computes the same
+                           rotations up to rounding): MPS_SVD_AUTO (default) the block kernel with Gram-matrix
+                           inner sweeps, one thread-block cluster per pair of 16-column blocks across the GPU,
+                           from 1024 columns on, else the tournament kernels; MPS_SVD_TOURNAMENT the
+                           cluster-resident / point-to-point tournament kernels only; MPS_SVD_GRAM the Gram
+                           block kernel wherever a layout fits (64 columns and more). */
+  int qr;               /* Householder QR in the update (complex64), bit flags: MPS_QR_MOVES (default) moves the
+                           orthogonality centre by QR ("Canonicalization" section; otherwise by a Jacobi
+                           orthogonalisation), MPS_QR_PRECONDITION runs the gate SVD on the triangular factor
+                           of theta (fewer sweeps, one QR more). */
 } mps_options;
 
 /* One record per two-qubit gate: bond size kept, truncation fidelity f, the

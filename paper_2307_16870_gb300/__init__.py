@@ -35,6 +35,8 @@ PURE, MIXED = 0, 1
 NAIVE, GLOBAL, NEAREST = 0, 1, 2
 FP64, TF32X3, FP32 = 0, 1, 2
 KEPT_RATIO, WANG_SQRT = 0, 1
+SVD_AUTO, SVD_TOURNAMENT, SVD_GRAM = 0, 1, 2
+QR_PRECONDITION, QR_MOVES = 1, 2
 
 OK, WARN_CHI_CAP = 0, 7
 
@@ -45,7 +47,8 @@ TC_AVAILABLE = True
 class MpsOptions(C.Structure):
     _fields_ = [("kind", C.c_int), ("f_min", C.c_double), ("n_2q", C.c_longlong), ("strategy", C.c_int),
                 ("chi_max", C.c_int), ("fixed_chi", C.c_int), ("precision", C.c_int), ("mixed_fid", C.c_int),
-                ("max_sweeps", C.c_int), ("log_truncations", C.c_int), ("vidal", C.c_int)]
+                ("max_sweeps", C.c_int), ("log_truncations", C.c_int), ("vidal", C.c_int),
+                ("svd_kernel", C.c_int), ("qr", C.c_int)]
 
 
 class BatchItem(C.Structure):
@@ -396,7 +399,7 @@ def mps_batch_run(circuits: list, concurrency: int = 4, keep: bool = False):
         it.target = float(c.get("target", -1.0))
         o = mps_default_options()
         for name in ("kind", "f_min", "n_2q", "strategy", "chi_max", "fixed_chi", "precision", "mixed_fid",
-                     "max_sweeps", "vidal"):
+                     "max_sweeps", "vidal", "svd_kernel", "qr"):
             if name in c:
                 setattr(o, name, c[name])
         o.log_truncations = int(c.get("log_truncations", 0))
@@ -428,12 +431,16 @@ class MPS:
     def __init__(self, n_qubits: int, kind: int = PURE, f_min: float = 1.0, n_2q: int = 0,
                  strategy: int = GLOBAL, chi_max: int = 0, fixed_chi: int = 0, precision: int = TF32X3,
                  mixed_fid: int = KEPT_RATIO, max_sweeps: int = 40, log_truncations: bool = True,
-                 stream: int = 0, vidal: bool = False):
+                 stream: int = 0, vidal: bool = False, svd_kernel: int | None = None, qr: int | None = None):
         o = mps_default_options()
         o.kind, o.f_min, o.n_2q, o.strategy = kind, f_min, n_2q, strategy
         o.chi_max, o.fixed_chi, o.precision, o.mixed_fid = chi_max, fixed_chi, precision, mixed_fid
         o.max_sweeps, o.log_truncations = max_sweeps, int(log_truncations)
         o.vidal = int(vidal)
+        if svd_kernel is not None:
+            o.svd_kernel = int(svd_kernel)
+        if qr is not None:
+            o.qr = int(qr)
         self.n = n_qubits
         self.kind = kind
         self.d = 2 if kind == PURE else 4

@@ -36,10 +36,10 @@ class Workspace:
     """Scratch and stream for the stateless update calls: a handle sized for chains of
     ``n_qubits`` sites with bonds up to ``chi_max``, on torch's current stream."""
 
-    def __init__(self, n_qubits: int, chi_max: int, precision: int = TF32X3):
+    def __init__(self, n_qubits: int, chi_max: int, precision: int = TF32X3, svd_kernel: int | None = None):
         self.stream = torch.cuda.current_stream()
         self.mps = MPS(max(n_qubits, 2), chi_max=chi_max, precision=precision, log_truncations=False,
-                       stream=self.stream.cuda_stream)
+                       stream=self.stream.cuda_stream, svd_kernel=svd_kernel)
         self.h = self.mps.h
         self.dtype = torch.complex128 if precision == FP64 else torch.complex64
 

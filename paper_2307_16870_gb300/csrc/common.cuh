@@ -70,6 +70,8 @@ struct DevCtrl {
   unsigned bar_gen;
   unsigned rot[3];
   unsigned pad_;
+  // wall-clock limit of every device-side wait, nanoseconds (0: kWaitNs)
+  unsigned long long wait_ns;
   // statistics accumulated over Jacobi launches (reset by the host)
   unsigned long long jac_sweeps;
   double jac_flops;
@@ -77,6 +79,19 @@ struct DevCtrl {
 
 // Bounded spin limit of every device-side wait (a few seconds at most).
 constexpr long long kSpinLimit = 20000000LL;
+
+// Wall-clock limit of the waits: %globaltimer nanoseconds, so the budget of a wait depends neither
+// on the SM clock nor on the cost of one poll.  DevCtrl::wait_ns overrides it per handle.
+constexpr unsigned long long kWaitNs = 2000000000ull;
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned long long wait_deadline(const DevCtrl* ctrl) {
+  const unsigned long long w = *(volatile const unsigned long long*)&ctrl->wait_ns;
+  return global_ns() + (w ? w : kWaitNs);
+}
 
 // Grid-wide barrier for a cooperative launch of nblocks CTAs.  Returns false
 // (and sets ST_TIMEOUT) if the wait exceeded kSpinLimit iterations; callers

@@ -365,10 +365,10 @@ struct Engine final : mps_state {
       if (mps_status s = reset_lambda()) return s;
     }
     if (std::is_same<R, float>::value) {
-      // EAMPS_QR bits: 1 the QR-preconditioned gate SVD, 2 the centre moves by QR (default 2:
-      // measured, the preconditioning saves about as many Jacobi sweeps as its QR costs)
-      const char* env = std::getenv("EAMPS_QR");
-      qr_mode = (env && *env) ? std::atoi(env) : 2;
+      // mps_options.qr bits: MPS_QR_PRECONDITION the QR-preconditioned gate SVD, MPS_QR_MOVES the
+      // centre moves by QR (default MPS_QR_MOVES: measured, the preconditioning saves about as
+      // many Jacobi sweeps as its QR costs)
+      qr_mode = o.qr;
       qr_on = (qr_mode & 3) != 0;
       qr_fit = qr_on ? qr_max_ctas() : 0;
       if (qr_fit <= 0) qr_on = false;
@@ -414,14 +414,16 @@ struct Engine final : mps_state {
     if (acc)
       if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
     if (c <= 1) return MPS_OK;
-    JacobiPlan plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count);
-    const int fit = plan.cluster > 0 ? plan.cluster : jacobi_max_ctas<R>(plan);
-    if (fit <= 0) return MPS_ERR_CUDA;
-    if (plan.nb / 2 > fit) {
-      plan = jacobi_plan<R>(l, c, acc, sm_count, fit);
-      if (plan.nb / 2 > fit) return MPS_ERR_ARG;
+    JacobiPlan plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count, opt.svd_kernel);
+    if (plan.gram_R == 0) {   // (the Gram layout is checked for residency when it is planned)
+      const int fit = plan.cluster > 0 ? plan.cluster : jacobi_max_ctas<R>(plan);
+      if (fit <= 0) return MPS_ERR_CUDA;
+      if (plan.nb / 2 > fit) {
+        plan = jacobi_plan<R>(l, c, acc, sm_count, fit, MPS_SVD_TOURNAMENT);
+        if (plan.nb / 2 > fit) return MPS_ERR_ARG;
+      }
     }
-    if (mps_status s = coop_ensure(plan.cluster > 0 ? plan.cluster : plan.nb / 2)) return s;
+    if (mps_status s = coop_ensure(jacobi_plan_ctas(plan))) return s;
     ++n_jac;
     if (in_move) ++n_jac_move;
     const int id = tbegin();
@@ -1227,6 +1229,8 @@ void mps_default_options(mps_options* o) {
   o->max_sweeps = 40;
   o->log_truncations = 1;
   o->vidal = 0;
+  o->svd_kernel = MPS_SVD_AUTO;
+  o->qr = MPS_QR_MOVES;
 }
 
 const char* mps_status_string(mps_status s) {
@@ -1252,7 +1256,8 @@ mps_status mps_create(mps_handle* out, int n_qubits, const mps_options* opt, voi
   if (opt->kind != MPS_PURE && opt->kind != MPS_MIXED) return MPS_ERR_ARG;
   if (!(opt->f_min > 0.0) || opt->strategy < 0 || opt->strategy > 2 || opt->chi_max < 0 || opt->fixed_chi < 0 ||
       opt->precision < 0 || opt->precision > 2 || opt->mixed_fid < 0 || opt->mixed_fid > 1 || opt->max_sweeps < 1 ||
-      opt->n_2q < 0 || opt->chi_max > 4096 || opt->vidal < 0 || opt->vidal > 1 ||
+      opt->n_2q < 0 || opt->chi_max > 4096 || opt->vidal < 0 || opt->vidal > 1 || opt->svd_kernel < 0 ||
+      opt->svd_kernel > 2 || opt->qr < 0 || opt->qr > 3 ||
       (opt->vidal && opt->kind != MPS_PURE))
     return MPS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;

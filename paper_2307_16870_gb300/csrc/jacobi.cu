@@ -882,11 +882,6 @@ const Variant* find_variant(int nw, int rpl, int ap) {
 
 namespace {
 
-int env_int(const char* name, int dflt) {
-  const char* v = std::getenv(name);
-  return (v && *v) ? std::atoi(v) : dflt;
-}
-
 // Rows per lane of the register-resident kernels for padded columns of L rows (0: too long).
 int rows_per_lane(int L) {
   for (int r : {4, 8, 12, 16, 24, 32})
@@ -911,23 +906,26 @@ int jacobi_max_ctas(const JacobiPlan& plan) {
 // Block width, CTA count and kernel variant for one SVD.
 //  * complex64 with columns of at most 1024 rows (accumulated rotations included): the
 //    register-resident kernel; one CTA when every column fits it, else about
-//    c / (2 w) CTAs with w = 8 columns per block (tuning overrides: EAMPS_JACOBI_NW,
-//    EAMPS_JACOBI_AP, EAMPS_JACOBI_SINGLE).
+//    c / (2 w) CTAs with w = 8 columns per block.
 //  * otherwise (complex128, longer columns): the shared-memory kernel.
 template <class R>
-JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas) {
+JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas, int kind) {
   JacobiPlan plan;
   const int L = l + (accumulate ? c : 0);
+  // block Jacobi with Gram-matrix inner sweeps over clusters across the GPU (jacobi_gram.cu)
+  if (std::is_same<R, float>::value && kind != kJacobiTournament && c >= (kind == kJacobiGram ? 64 : kGramMinCols) &&
+      jacobi_gram_plan(l, c, accumulate, std::min(sm_count, max_ctas), plan))
+    return plan;
   const size_t budget = 200 * 1024;
   // register-resident kernels: padded columns (W rows start at l rounded up to 32)
   const int Lreg = accumulate ? ((l + 31) & ~31) + c : l;
   const int rpl = rows_per_lane(Lreg);
   const size_t col_bytes = (size_t)32 * rpl * sizeof(cplx<R>);
-  if (std::is_same<R, float>::value && rpl > 0 && rpl <= 16 && env_int("EAMPS_JACOBI_CLUSTER", 1)) {
+  if (std::is_same<R, float>::value && rpl > 0 && rpl <= 16) {
     // whole matrix in one cluster of at most 16 CTAs with 8 warps each (w = 8), i.e. up to 256
     // columns; wider blocks (16 warps) were measured slower than the point-to-point kernel on
     // more SMs, because a step's latency grows with the warps that share an SM
-    const int nw = env_int("EAMPS_JACOBI_CNW", 8);
+    const int nw = 8;
     const Variant* v = find_cluster_variant(nw, rpl);
     if (v) {
       const int w = v->nw;
@@ -948,7 +946,7 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
   if (std::is_same<R, float>::value && rpl > 0) {
     const int target = std::max(1, std::min(sm_count, max_ctas));
     // single CTA: the widest variant whose columns fit
-    const int single_max = env_int("EAMPS_JACOBI_SINGLE", 64);
+    const int single_max = 64;
     const Variant* v = nullptr;
     int w = 0;
     if (c <= single_max) {
@@ -966,7 +964,7 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
     }
     int nb = 2;
     if (!v) {
-      const int nw = env_int("EAMPS_JACOBI_NW", 8), ap = env_int("EAMPS_JACOBI_AP", 1);
+      const int nw = 8, ap = 1;
       v = find_variant(nw, rpl, ap);
       if (!v) v = find_variant(8, rpl, 1);
       w = v->nw * v->ap;
@@ -1023,6 +1021,11 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
                           cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cplx<R>* xch,
                           size_t xch_cap, unsigned* flags, int flags_cap, cudaStream_t st) {
   if (c <= 1) return cudaSuccess;   // a single column is already orthogonal
+  if (plan.gram_R > 0) {
+    if constexpr (std::is_same<R, float>::value)
+      return jacobi_gram_launch(plan, X, ldx, l, c, W, ldw, max_sweeps, ctrl, xch, xch_cap, flags, flags_cap, st);
+    return cudaErrorInvalidValue;
+  }
   if ((size_t)2 * plan.nb * plan.w * (size_t)plan.ld > xch_cap || plan.nb > flags_cap) return cudaErrorInvalidValue;
   cudaError_t e = allow_dynamic_smem(plan.fn);
   if (e != cudaSuccess) return e;
@@ -1063,8 +1066,8 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
   return cudaLaunchCooperativeKernel(plan.fn, dim3(P), dim3(plan.threads), args, plan.smem, st);
 }
 
-template JacobiPlan jacobi_plan<float>(int, int, bool, int, int);
-template JacobiPlan jacobi_plan<double>(int, int, bool, int, int);
+template JacobiPlan jacobi_plan<float>(int, int, bool, int, int, int);
+template JacobiPlan jacobi_plan<double>(int, int, bool, int, int, int);
 template cudaError_t jacobi_launch<float>(const JacobiPlan&, cplx<float>*, long long, int, int, cplx<float>*,
                                           long long, int, DevCtrl*, cplx<float>*, size_t, unsigned*, int,
                                           cudaStream_t);

@@ -64,9 +64,19 @@ struct JacobiPlan {
   int threads = 256;
   int cluster = 0;           // > 0: cluster-resident kernel, one cluster of this many CTAs
   int ld = 0;                // column stride (complex entries) in shared memory and the exchange slots
+  int gram_R = 0;            // > 0: block Jacobi with Gram-matrix inner sweeps (jacobi_gram.cu), one
+                             // cluster of gram_R CTAs per slot of two 16-column blocks, nb / 2 slots
+  int gram_mr = 0;           // rows of the stacked [X; W] held by each CTA of that kernel
 };
+// kind: kJacobiAuto (the Gram-matrix block kernel from kGramMinCols columns on, else the
+// tournament kernels), kJacobiTournament (the cluster / point-to-point kernels only), kJacobiGram
+// (the Gram-matrix block kernel whenever a layout fits, from 64 columns on).  Measured on GB300
+// (complex64, square theta): the two layouts take the same time at 512 columns (7.7 ms, 13 sweeps)
+// and the Gram kernel wins at 1024 (21.2 ms against 24.9 ms); below 512 the tournament kernels win.
+enum { kJacobiAuto = 0, kJacobiTournament = 1, kJacobiGram = 2 };
+constexpr int kGramMinCols = 1024;
 template <class R>
-JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas);
+JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas, int kind = kJacobiAuto);
 // xch: exchange slots of the multi-CTA kernels (2 * nb * w * plan.ld complex entries at
 // most xch_cap); flags: nb position flags (at most flags_cap).
 template <class R>
@@ -74,6 +84,17 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
                           cplx<R>* W, long long ldw, int max_sweeps, DevCtrl* ctrl, cplx<R>* xch,
                           size_t xch_cap, unsigned* flags, int flags_cap, cudaStream_t st);
 template <class R> int jacobi_max_ctas(const JacobiPlan& plan);
+// CTAs of one launch of the plan (all co-resident: they wait on one another).
+inline int jacobi_plan_ctas(const JacobiPlan& plan) {
+  if (plan.gram_R > 0) return plan.nb / 2 * plan.gram_R;
+  return plan.cluster > 0 ? plan.cluster : plan.nb / 2;
+}
+// Block one-sided Jacobi with Gram-matrix inner sweeps (complex64, c >= 64 columns): fills plan
+// and returns true when a layout of at most max_ctas co-resident CTAs exists.
+bool jacobi_gram_plan(int l, int c, bool accumulate, int max_ctas, JacobiPlan& plan);
+cudaError_t jacobi_gram_launch(const JacobiPlan& plan, float2* X, long long ldx, int l, int c, float2* W,
+                               long long ldw, int max_sweeps, DevCtrl* ctrl, float2* xch, size_t xch_cap,
+                               unsigned* flags, int flags_cap, cudaStream_t st);
 
 // ------------------------------------------------------------ CUDA-core GEMM
 // C = alpha * op(A) * op(B); op(A)[i,k] = A[i*a_rs + k*a_cs] (conjugated if conjA).

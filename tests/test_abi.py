@@ -42,9 +42,12 @@ def test_status_strings_and_defaults():
 
 def test_options_struct_layout_matches_header():
     import paper_2307_16870_gb300 as E
-    # int, double, long long, 7 ints -> 4 + 4(pad) + 8 + 8 + 7*4 = 52 -> 56 with tail padding
-    assert ctypes.sizeof(E.MpsOptions) == 56
+    # int, double, long long, 9 ints -> 4 + 4(pad) + 8 + 8 + 9*4 = 60 -> 64 with tail padding
+    assert ctypes.sizeof(E.MpsOptions) == 64
     assert ctypes.sizeof(E.TruncRecord) == 48
+    # the library fills the struct: its last fields land where the binding reads them
+    o = E.mps_default_options()
+    assert (o.max_sweeps, o.log_truncations, o.vidal, o.svd_kernel, o.qr) == (40, 1, 0, E.SVD_AUTO, E.QR_MOVES)
 
 
 def test_superop_helper_matches_oracle():

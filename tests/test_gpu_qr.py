@@ -73,16 +73,16 @@ def test_qr_rejects_too_many_rows():
         E.mps_qr_c64(513, 4, x.data_ptr(), 513)
 
 
-@pytest.mark.parametrize("mode", ["0", "1", "2", "3"])
-def test_circuit_with_qr_modes_matches_oracle(mode, monkeypatch):
-    """EAMPS_QR bits: 1 the preconditioned gate SVD, 2 the QR centre moves (0: Jacobi only)."""
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_circuit_with_qr_modes_matches_oracle(mode):
+    """mps_options.qr bits: QR_PRECONDITION the preconditioned gate SVD, QR_MOVES the QR centre
+    moves (0: Jacobi only)."""
     import workloads as W
     from oracle import textbook_mps as T
     from oracle import statevector as SV
-    monkeypatch.setenv("EAMPS_QR", mode)
     n = 12
     circ = W.brickwork_circuit(n, 10, 77)
-    m = E.MPS(n, f_min=0.97, n_2q=circ.n_2q, precision=E.TF32X3, log_truncations=False)
+    m = E.MPS(n, f_min=0.97, n_2q=circ.n_2q, precision=E.TF32X3, log_truncations=False, qr=mode)
     m.run(circ.gates())
     o = T.TextbookMPS(n, f_min=0.97, n_2q=circ.n_2q)
     for q, u in circ.gates():
@@ -95,7 +95,7 @@ def test_circuit_with_qr_modes_matches_oracle(mode, monkeypatch):
     f_orc = abs(np.vdot(psi, o.to_statevector())) ** 2
     assert abs(f_true - f_orc) < 1e-4
     st = m.stats()
-    if mode == "0":
+    if mode == 0:
         assert st["qr_launches"] == 0
     else:
         assert st["qr_launches"] > 0
