@@ -97,10 +97,11 @@ __device__ __forceinline__ bool rot_params_fused(float a, float b, float gr, flo
 }
 
 // Orthogonalise columns x and y (length L, of which the first l enter the
-// inner products).  Returns 1 if a rotation was applied.
+// inner products).  Returns 0 when no rotation was applied, 1 for a rotation of a pair
+// whose cosine was at most tol_stop, 2 for a larger one.
 template <class R>
 __device__ __forceinline__ int rotate_pair(cplx<R>* __restrict__ x, cplx<R>* __restrict__ y, int l, int L,
-                                           R tol, int lane) {
+                                           R tol, R tol_stop, int lane) {
   R a = 0, b = 0, gr = 0, gi = 0;
   for (int i = lane; i < l; i += 32) {
     cplx<R> u = x[i], v = y[i];
@@ -112,6 +113,7 @@ __device__ __forceinline__ int rotate_pair(cplx<R>* __restrict__ x, cplx<R>* __r
   a = warp_sum(a); b = warp_sum(b); gr = warp_sum(gr); gi = warp_sum(gi);
   R cs, sn, er, ei;
   if (!rot_params<R>(a, b, gr, gi, tol, cs, sn, er, ei)) return 0;
+  const int large = (gr * gr + gi * gi > tol_stop * tol_stop * a * b) ? 2 : 1;
   // x' = cs x - sn e^{-i phi} y ;  y' = sn e^{i phi} x + cs y
   for (int i = lane; i < L; i += 32) {
     cplx<R> u = x[i], v = y[i];
@@ -120,7 +122,7 @@ __device__ __forceinline__ int rotate_pair(cplx<R>* __restrict__ x, cplx<R>* __r
     x[i] = mk<R>(cs * u.x - sn * cyr, cs * u.y - sn * cyi);
     y[i] = mk<R>(sn * exr + cs * v.x, sn * exi + cs * v.y);
   }
-  return 1;
+  return large;
 }
 
 template <class R>
@@ -128,6 +130,7 @@ struct JArgs {
   cplx<R>* X; long long ldx; int l; int c;
   cplx<R>* W; long long ldw;
   int w; int nb; int max_sweeps; R tol;
+  R tol_stop;          // a sweep whose largest pair cosine is at most this ends the iteration
   DevCtrl* ctrl;
   cplx<R>* xch;        // exchange slots: [2 parities][nb positions][w columns][L]
   unsigned* flags;     // per position: 1 + the last round whose block was published
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JArgs<R> p) {
   const int L = p.l + (p.W ? p.c : 0);
   cplx<R>* slots = reinterpret_cast<cplx<R>*>(smem_raw);
   int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * L);
-  __shared__ unsigned rot_s;
+  __shared__ unsigned rot_s, big_s;   // rotations of this CTA in the sweep, those above tol_stop
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int cta = blockIdx.x;
   const int wpad = w + (w & 1);   // even player count for the intra-block tournament
@@ -289,13 +292,13 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JArgs<R> p) {
   int sweep = 0;
   bool converged = false;
   for (sweep = 0; sweep < p.max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) rot_s = 0;
+    if (threadIdx.x == 0) { rot_s = 0; big_s = 0; }
     __syncthreads();
     for (int r = 0; r < nb - 1; ++r) {
       bA = rr_player(nb, r, cta);
       bB = rr_player(nb, r, nb - 1 - cta);
       if (P > 1 || !loaded) { load_pair(p, slots, gcol, L, bA, bB); loaded = true; }
-      unsigned my_rot = 0;
+      unsigned my_rot = 0, my_big = 0;
       if (r == 0) {
         // pairs inside each block: round robin over wpad players, both blocks at once
         const int half = wpad / 2;
@@ -306,7 +309,10 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JArgs<R> p) {
             if (s1 >= w || s2 >= w) continue;
             s1 += blk * w; s2 += blk * w;
             if (gcol[s1] < 0 || gcol[s2] < 0) continue;
-            my_rot += rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, p.l, L, p.tol, lane);
+            const int rc = rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, p.l, L, p.tol,
+                                          p.tol_stop, lane);
+            my_rot += rc != 0;
+            my_big += rc == 2;
           }
           __syncthreads();
         }
@@ -316,21 +322,25 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JArgs<R> p) {
         for (int i = warp; i < w; i += nwarps) {
           int s1 = i, s2 = w + (i + t) % w;
           if (gcol[s1] < 0 || gcol[s2] < 0) continue;
-          my_rot += rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, p.l, L, p.tol, lane);
+          const int rc = rotate_pair<R>(slots + (long long)s1 * L, slots + (long long)s2 * L, p.l, L, p.tol,
+                                        p.tol_stop, lane);
+          my_rot += rc != 0;
+          my_big += rc == 2;
         }
         __syncthreads();
       }
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
+      if (lane == 0 && my_big) atomicAdd(&big_s, my_big);
       if (P > 1) {
         store_pair(p, slots, gcol, L);
-        if (r == nb - 2 && threadIdx.x == 0) atomicAdd(&p.ctrl->rot[sweep % 3], rot_s);
+        if (r == nb - 2 && threadIdx.x == 0) atomicAdd(&p.ctrl->rot[sweep % 3], big_s);
         if (!grid_barrier(p.ctrl, P)) return;
         if (r == 0 && cta == 0 && threadIdx.x == 0) p.ctrl->rot[(sweep + 1) % 3] = 0u;
       } else {
         __syncthreads();
       }
     }
-    unsigned total = (P > 1) ? *(volatile unsigned*)&p.ctrl->rot[sweep % 3] : rot_s;
+    unsigned total = (P > 1) ? *(volatile unsigned*)&p.ctrl->rot[sweep % 3] : big_s;
     if (threadIdx.x == 0) rot_total += rot_s;
     __syncthreads();
     if (total == 0) { converged = true; break; }
@@ -442,8 +452,8 @@ __device__ __forceinline__ void warp_allreduce(float (&v)[N], int lane) {
 // registers; at step t it takes B column w + (ia + t) mod w, which warp + 1 (mod NW)
 // released at step t - 1.  Returns the rotations applied by this warp.
 template <int NW, int RPL, int AP>
-__device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int w, int kl, float tol, int lane,
-                                                int warp) {
+__device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int w, int kl, float tol, float tol_stop,
+                                                int lane, int warp, unsigned& big) {
   constexpr int ld = 32 * RPL;
   float2 A[AP][RPL], B[AP][RPL];
   int ib[AP];
@@ -495,6 +505,8 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
     for (int a = 0; a < AP; ++a) {
       float cs, al, be;
       if (rot_params_fused(s[4 * a], s[4 * a + 1], s[4 * a + 2], s[4 * a + 3], tol, cs, al, be)) {
+        big += (s[4 * a + 2] * s[4 * a + 2] + s[4 * a + 3] * s[4 * a + 3] >
+                tol_stop * tol_stop * s[4 * a] * s[4 * a + 1]) ? 1u : 0u;
         // x' = cs x - sn e^{-i phi} y = cs x - al y - be (y.im, -y.re)
         // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al + i be = sn e^{i phi}
         const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
@@ -529,7 +541,7 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
 // Pairs inside each of the two blocks (round 0 of a sweep): round robin over wpad players,
 // both blocks at once, one warp per pair.
 __device__ __forceinline__ unsigned intra_phase(float2* slots, const int* gcol, int w, int ld, int lrows, float tol,
-                                                int lane, int warp, int nwarps) {
+                                                float tol_stop, int lane, int warp, int nwarps, unsigned& big) {
   const int wpad = w + (w & 1);
   const int half = wpad / 2;
   unsigned my_rot = 0;
@@ -540,7 +552,10 @@ __device__ __forceinline__ unsigned intra_phase(float2* slots, const int* gcol, 
       if (s1 >= w || s2 >= w) continue;
       s1 += blk * w; s2 += blk * w;
       if (gcol[s1] < 0 || gcol[s2] < 0) continue;
-      my_rot += rotate_pair<float>(slots + (long long)s1 * ld, slots + (long long)s2 * ld, lrows, ld, tol, lane);
+      const int rc = rotate_pair<float>(slots + (long long)s1 * ld, slots + (long long)s2 * ld, lrows, ld, tol,
+                                        tol_stop, lane);
+      my_rot += rc != 0;
+      big += rc == 2;
     }
     __syncthreads();
   }
@@ -571,7 +586,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
   const int kl = p.W ? lw / 32 : RPL;
   float2* slots = reinterpret_cast<float2*>(smem_raw);
   int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * ld);
-  __shared__ unsigned rot_s;
+  __shared__ unsigned rot_s, big_s;   // rotations in the sweep, those above tol_stop (the vote)
   __shared__ unsigned total_s;
   __shared__ __align__(8) uint64_t xbar;   // completion of the incoming bulk copies
   __shared__ int xok_s;
@@ -598,7 +613,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
   __syncthreads();
 
   for (sweep = 0; sweep < p.max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) rot_s = 0;
+    if (threadIdx.x == 0) { rot_s = 0; big_s = 0; }
     __syncthreads();
     for (int r = 0; r < nb - 1; ++r, ++rnd) {
       if (rnd > 0 && P > 1) {
@@ -641,10 +656,11 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         }
         __syncthreads();
       }
-      unsigned my_rot = 0;
-      if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, lane, warp, NW);
-      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, lane, warp);
+      unsigned my_rot = 0, my_big = 0;
+      if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, p.tol_stop, lane, warp, NW, my_big);
+      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, p.tol_stop, lane, warp, my_big);
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
+      if (lane == 0 && my_big) atomicAdd(&big_s, my_big);
       // shared-memory writes above must be visible to the bulk stores below
       if (bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -681,7 +697,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
     // convergence vote over all CTAs: one counter barrier per sweep
     if (P > 1) {
       if (threadIdx.x == 0) {
-        atomicAdd(&p.ctrl->rot[sweep % 3], rot_s);
+        atomicAdd(&p.ctrl->rot[sweep % 3], big_s);
         const unsigned old = atom_add_release(&p.ctrl->bar_count, 1u);
         total_s = (old / (unsigned)P + 1u) * (unsigned)P;   // arrivals that complete this barrier
       }
@@ -693,7 +709,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
       }
       __syncthreads();
     } else {
-      if (threadIdx.x == 0) total_s = rot_s;
+      if (threadIdx.x == 0) total_s = big_s;
       __syncthreads();
     }
     if (threadIdx.x == 0) rot_total += rot_s;
@@ -731,8 +747,8 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
   const int kl = p.W ? lw / 32 : RPL;
   float2* slots = reinterpret_cast<float2*>(smem_raw);
   int* gcol = reinterpret_cast<int*>(slots + (long long)2 * w * ld);
-  __shared__ unsigned rot_s;
-  __shared__ unsigned rot_slot[2];
+  __shared__ unsigned rot_s, big_s, vote_s;
+  __shared__ unsigned rot_slot[2], big_slot[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cta = (int)cluster.block_rank();
   const int pos[2] = {cta, nb - 1 - cta};
@@ -756,22 +772,23 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
     const int g = pos[s / w] * w + (s % w);
     gcol[s] = g < p.c ? g : -1;
   }
-  if (threadIdx.x == 0) { rot_slot[0] = 0; rot_slot[1] = 0; }
+  if (threadIdx.x == 0) { rot_slot[0] = 0; rot_slot[1] = 0; big_slot[0] = 0; big_slot[1] = 0; vote_s = 0; }
   __syncthreads();
   for (int s = warp; s < 2 * w; s += NW) fill_column<RPL>(slots + (long long)s * ld, p, gcol[s], lw, lane);
   __syncthreads();
 
   for (sweep = 0; sweep < p.max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) rot_s = 0;
+    if (threadIdx.x == 0) { rot_s = 0; big_s = 0; }
     __syncthreads();
     for (int r = 0; r < nb - 1; ++r) {
-      unsigned my_rot = 0;
-      if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, lane, warp, NW);
-      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, lane, warp);
+      unsigned my_rot = 0, my_big = 0;
+      if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, p.tol_stop, lane, warp, NW, my_big);
+      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, p.tol_stop, lane, warp, my_big);
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
+      if (lane == 0 && my_big) atomicAdd(&big_s, my_big);
       __syncthreads();
       const bool last = (r == nb - 2);
-      if (last && threadIdx.x == 0) rot_slot[sweep & 1] = rot_s;
+      if (last && threadIdx.x == 0) { rot_slot[sweep & 1] = rot_s; big_slot[sweep & 1] = big_s; }
       if (P > 1) {
         cluster.sync();   // every CTA finished the round: its shared blocks are final
         // Two phases, one block staged in registers at a time.  Phase 1: CTAs 1..P-1 take the
@@ -792,7 +809,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
         }
         unsigned vote = 0;
         if (last && threadIdx.x == 0) {
-          for (int q = 0; q < P; ++q) vote += cluster.map_shared_rank(rot_slot, q)[sweep & 1];
+          for (int q = 0; q < P; ++q) vote += cluster.map_shared_rank(big_slot, q)[sweep & 1];
         }
         cluster.sync();   // phase-1 sources read
         if (cta != 0) {
@@ -822,12 +839,12 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
           const int g = rr_player(nb, rn, pos[s / w]) * w + (s % w);
           gcol[s] = g < p.c ? g : -1;
         }
-        if (last && threadIdx.x == 0) rot_s = vote;
+        if (last && threadIdx.x == 0) vote_s = vote;
         __syncthreads();
       }
     }
     if (threadIdx.x == 0) rot_total += (P > 1) ? rot_slot[sweep & 1] : rot_s;
-    const unsigned total = rot_s;   // P > 1: the cluster-wide vote; P == 1: this CTA's count
+    const unsigned total = (P > 1) ? vote_s : big_s;   // rotations above tol_stop: cluster-wide or this CTA's
     __syncthreads();
     if (total == 0) { converged = true; break; }
   }
@@ -1038,6 +1055,9 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
   a.X = X; a.ldx = ldx; a.l = l; a.c = c; a.W = W; a.ldw = ldw;
   a.w = plan.w; a.nb = plan.nb; a.max_sweeps = max_sweeps;
   a.tol = R(4) * std::sqrt(R(std::max(l, 1))) * Eps<R>::v;
+  // quadratic convergence: after a sweep whose pair cosines were all at most sqrt(tol), the next
+  // sweep's are at the rounding level, so that sweep is not run
+  a.tol_stop = std::sqrt(a.tol);
   a.ctrl = ctrl;
   a.xch = xch;
   a.flags = flags;

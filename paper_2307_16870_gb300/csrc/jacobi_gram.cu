@@ -54,6 +54,7 @@ struct GArgs {
   float2* W; long long ldw;
   int nb; int S; int R; int mr;
   int max_sweeps; float tol;
+  float tol_stop;     // a sweep whose largest pair cosine is at most this ends the iteration
   DevCtrl* ctrl;
   float2* xbuf;       // [S][2 directions][R][mr rows x 16 columns, then the block's 16 x 16 Gram]
   unsigned* flags;    // [S][2][R] release flags, then [S][2][R] block ids
@@ -119,7 +120,7 @@ __device__ __forceinline__ void column_pair(bool rr, int t, int j, int& u, int& 
 // Rotation of columns with squared norms a, b and inner product g = <x_p, x_q> that makes them
 // orthogonal, and the norms after it (the larger one grows by 2|g|^2 / D, the smaller one shrinks by
 // as much: no cancellation).  Identity when the pair is orthogonal to the tolerance.
-__device__ __forceinline__ Prm make_prm(float a, float b, float2 g, float tol, int& rot) {
+__device__ __forceinline__ Prm make_prm(float a, float b, float2 g, float tol, float tol_stop, int& rot, int& big) {
   Prm P;
   P.cs = 1.f; P.sr = 0.f; P.si = 0.f; P.dp = a; P.dq = b; P.pad = 0.f;
   const float g2 = g.x * g.x + g.y * g.y;
@@ -133,6 +134,7 @@ __device__ __forceinline__ Prm make_prm(float a, float b, float2 g, float tol, i
   P.cs = D * r;
   P.sr = s2 * g.x;
   P.si = s2 * g.y;
+  big += (g2 > tol_stop * tol_stop * a * b) ? 1 : 0;
   const float del = __fdividef(2.f * g2, D);
   if (u >= 0.f) { P.dp = a - del; P.dq = b + del; }
   else { P.dp = a + del; P.dq = b - del; }
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_gram_kernel(GArgs p) {
   float2* rbuf = pbuf + kNE;                                 // [kNE] reduce-scattered sums (cluster-read)
   Prm* ring = reinterpret_cast<Prm*>(rbuf + kNE);            // [3][16] rotations of consecutive steps
   __shared__ int hdr[4];                                     // [2] abort words, [2] sweep decisions
-  __shared__ unsigned rot_s;
+  __shared__ unsigned rot_s, big_s;
   __shared__ int ok_s, blk_s;
 
   const int R = p.R, S = p.S, nb = p.nb;
@@ -206,13 +208,13 @@ __global__ void __launch_bounds__(kThreads) jacobi_gram_kernel(GArgs p) {
     Xs[r * kXLD + j] = load_elem(p, ((j < kBW) ? blk0 : blk1) * kBW + (j & 15), rowbase + r);
   }
 
-  int my_rot = 0;
+  int my_rot = 0, my_big = 0;   // rotations decided by this thread, those above tol_stop
   int local_abort = 0;
   unsigned long long rot_total = 0;
   bool converged = false, aborted = false;
   unsigned gr = 0;
   int sweep = 0;
-  if (tid == 0) rot_s = 0;
+  if (tid == 0) { rot_s = 0; big_s = 0; }
   __syncthreads();
 
   for (sweep = 0; sweep < p.max_sweeps && !aborted; ++sweep) {
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(kThreads) jacobi_gram_kernel(GArgs p) {
         if (tid < 16) {
           int pp, qq;
           pair_members(rr, 0, tid, pp, qq);
-          ring[tid] = make_prm(G[pp * kGLD + pp].x, G[qq * kGLD + qq].x, gget(G, pp, qq), p.tol, my_rot);
+          ring[tid] = make_prm(G[pp * kGLD + pp].x, G[qq * kGLD + qq].x, gget(G, pp, qq), p.tol, p.tol_stop, my_rot,
+                               my_big);
         }
         __syncthreads();
         for (int t = 0; t <= nsteps; ++t) {
@@ -370,8 +373,9 @@ __global__ void __launch_bounds__(kThreads) jacobi_gram_kernel(GArgs p) {
                       const float di = h ? Pu.dq : Pu.dp;
                       const float dj = (pt == c) ? Pv.dp : Pv.dq;
                       const float2 gij = h ? ((pt == c) ? nbc : nbd) : ((pt == c) ? nac : nad);
-                      nxt[u2] = role2 == 0 ? make_prm(di, dj, gij, p.tol, my_rot)
-                                           : make_prm(dj, di, make_float2(gij.x, -gij.y), p.tol, my_rot);
+                      nxt[u2] = role2 == 0
+                                    ? make_prm(di, dj, gij, p.tol, p.tol_stop, my_rot, my_big)
+                                    : make_prm(dj, di, make_float2(gij.x, -gij.y), p.tol, p.tol_stop, my_rot, my_big);
                     }
                   }
                 }
@@ -460,13 +464,16 @@ __global__ void __launch_bounds__(kThreads) jacobi_gram_kernel(GArgs p) {
     if (aborted) break;
     // ---- convergence vote: rotation count of every slot (rank 0 of each cluster), one counter barrier
     if (my_rot) atomicAdd(&rot_s, (unsigned)my_rot);
+    if (my_big) atomicAdd(&big_s, (unsigned)my_big);
     my_rot = 0;
+    my_big = 0;
     __syncthreads();
     if (tid == 0) {
       int decision = 0;   // 0: continue, 1: converged, 2: leave
-      const unsigned mine = rot_s;
+      const unsigned mine = big_s;
+      rot_total += rot_s;
       rot_s = 0;
-      rot_total += mine;
+      big_s = 0;
       if (nctas > 1) {
         if (rank == 0) atomicAdd(&p.ctrl->rot[sweep % 3], mine);
         const unsigned old = atom_add_release_u32(&p.ctrl->bar_count, 1u);
@@ -603,6 +610,7 @@ cudaError_t jacobi_gram_launch(const JacobiPlan& plan, float2* X, long long ldx,
   a.nb = plan.nb; a.S = S; a.R = R; a.mr = plan.gram_mr;
   a.max_sweeps = max_sweeps;
   a.tol = 4.f * std::sqrt((float)std::max(l, 1)) * FLT_EPSILON;
+  a.tol_stop = std::sqrt(a.tol);   // as the tournament kernels: the quadratic phase ends one sweep early
   a.ctrl = ctrl;
   a.xbuf = xch;
   a.flags = flags;
