@@ -182,15 +182,32 @@ mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, co
 mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
                                   double target, int concurrency);
 
-/* Failure-detection self-test: one device thread waits, in the form every
- * waiting kernel of the library uses (acquire load, back-off, iteration
- * limit), for a flag that nothing sets.  After `spins` iterations (1 <= spins
- * <= 2^31; 10^6 take well under a second) it records the timeout in the
- * handle's status word and returns: no trap, no fault, the context stays
- * usable.  Returns MPS_ERR_TIMEOUT; the handle then stays in the failed state
- * until mps_reset, like after any device-side timeout.
- * Errors: MPS_ERR_ARG (spins out of range), MPS_ERR_CUDA. */
-mps_status mps_selftest_wait(mps_handle h, long long spins);
+/* Failure-detection self-test (no trap, no fault: a signal is withheld and a
+ * bounded wait runs out).  Every device-side wait of the library gives up at a
+ * wall-clock deadline (2 s by default); this call sets the handle's limit to
+ * wait_ns (10^3 <= wait_ns <= 2*10^10) and runs one of:
+ *   MPS_SELFTEST_FLAG        one thread waits for a flag that nothing sets;
+ *   MPS_SELFTEST_JACOBI      the point-to-point tournament Jacobi kernel (18
+ *                            CTAs on a 64 x 288 matrix), CTA 0 withholding its
+ *                            block releases, so its neighbours' waits run out
+ *                            and every CTA returns;
+ *   MPS_SELFTEST_GRAM        the Gram-matrix block Jacobi kernel (64 x 128,
+ *                            clusters of CTAs), slot 0 withholding its block
+ *                            releases: the clusters agree on leaving at their
+ *                            next cluster barrier;
+ *   MPS_SELFTEST_GEMM        the tensor-core contraction (128 x 128 x 64) with
+ *                            CTA (0, 0)'s operand loads withheld: its MMA
+ *                            issuer's wait runs out, every role returns and the
+ *                            tensor memory is released.
+ * The kernel records the timeout in the handle's status word and returns.
+ * Returns MPS_ERR_TIMEOUT; the handle then stays in the failed state until
+ * mps_reset (which also restores the default limit), like after any
+ * device-side timeout.  Other handles are not affected.  The multi-CTA forms
+ * need a complex64 handle (MPS_SELFTEST_GEMM: MPS_TF32X3).
+ * Errors: MPS_ERR_ARG (site or wait_ns out of range, wrong precision),
+ * MPS_ERR_OOM, MPS_ERR_CUDA. */
+enum { MPS_SELFTEST_FLAG = 0, MPS_SELFTEST_JACOBI = 1, MPS_SELFTEST_GRAM = 2, MPS_SELFTEST_GEMM = 3 };
+mps_status mps_selftest_timeout(mps_handle h, int site, long long wait_ns);
 
 /* ---- Differentiable two-site update (stateless; the paper differentiates nothing) ----
  * These three calls run the steps of one two-site update (Eq. svd and the cut

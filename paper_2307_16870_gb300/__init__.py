@@ -28,7 +28,7 @@ __all__ = [
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
     "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap", "mps_qr_c64",
     "mps_apply_layer_device", "mps_gemm_device", "mps_tsvd_device", "mps_tsvd_backward_device",
-    "mps_selftest_wait",
+    "mps_selftest_timeout",
 ]
 
 PURE, MIXED = 0, 1
@@ -37,6 +37,7 @@ FP64, TF32X3, FP32 = 0, 1, 2
 KEPT_RATIO, WANG_SQRT = 0, 1
 SVD_AUTO, SVD_TOURNAMENT, SVD_GRAM = 0, 1, 2
 QR_PRECONDITION, QR_MOVES = 1, 2
+SELFTEST_FLAG, SELFTEST_JACOBI, SELFTEST_GRAM, SELFTEST_GEMM = 0, 1, 2, 3
 
 OK, WARN_CHI_CAP = 0, 7
 
@@ -136,7 +137,7 @@ def load(path: str | None = None):
                                       C.POINTER(C.c_double)]),
         "mps_tsvd_backward_device": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
-        "mps_selftest_wait": (C.c_int, [H, C.c_longlong]),
+        "mps_selftest_timeout": (C.c_int, [H, C.c_int, C.c_longlong]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -246,9 +247,10 @@ def mps_tsvd_backward_device(h: int, m: int, n: int, k: int, u: int, s: int, v: 
                   "mps_tsvd_backward_device")
 
 
-def mps_selftest_wait(h: int, spins: int = 1000000) -> int:
-    """Failure-detection self-test: a bounded device wait that runs out (see include/eamps.h)."""
-    return _check(load().mps_selftest_wait(C.c_void_p(h), int(spins)), "mps_selftest_wait")
+def mps_selftest_timeout(h: int, site: int = 0, wait_ns: int = 50_000_000) -> int:
+    """Failure-detection self-test: a withheld signal makes a bounded device wait run out
+    (site: SELFTEST_FLAG, SELFTEST_JACOBI, SELFTEST_GRAM, SELFTEST_GEMM; see include/eamps.h)."""
+    return _check(load().mps_selftest_timeout(C.c_void_p(h), int(site), int(wait_ns)), "mps_selftest_timeout")
 
 
 def mps_qr_c64(l: int, c: int, x_ptr: int, ldx: int, q_ptr: int = 0, ldq: int = 0, stream: int = 0) -> int:

@@ -72,13 +72,13 @@ struct DevCtrl {
   unsigned pad_;
   // wall-clock limit of every device-side wait, nanoseconds (0: kWaitNs)
   unsigned long long wait_ns;
+  // failure self-test only (mps_selftest_timeout): which multi-CTA kernel withholds one signal
+  int test_fault;
+  int pad2_;
   // statistics accumulated over Jacobi launches (reset by the host)
   unsigned long long jac_sweeps;
   double jac_flops;
 };
-
-// Bounded spin limit of every device-side wait (a few seconds at most).
-constexpr long long kSpinLimit = 20000000LL;
 
 // Wall-clock limit of the waits: %globaltimer nanoseconds, so the budget of a wait depends neither
 // on the SM clock nor on the cost of one poll.  DevCtrl::wait_ns overrides it per handle.
@@ -94,8 +94,8 @@ __device__ __forceinline__ unsigned long long wait_deadline(const DevCtrl* ctrl)
 }
 
 // Grid-wide barrier for a cooperative launch of nblocks CTAs.  Returns false
-// (and sets ST_TIMEOUT) if the wait exceeded kSpinLimit iterations; callers
-// then return without further waits.
+// (and sets ST_TIMEOUT) if the wait passed its wall-clock deadline or another
+// wait of the handle gave up; callers then return without further waits.
 __device__ __forceinline__ bool grid_barrier(DevCtrl* ctrl, unsigned nblocks) {
   __shared__ int ok_s;
   __syncthreads();
@@ -110,10 +110,14 @@ __device__ __forceinline__ bool grid_barrier(DevCtrl* ctrl, unsigned nblocks) {
       __threadfence();
       atomicAdd(&ctrl->bar_gen, 1u);
     } else {
-      long long spins = 0;
+      const unsigned long long end = wait_deadline(ctrl);
       while (*vgen == g) {
         __nanosleep(32);
-        if (++spins > kSpinLimit) { atomicOr(&ctrl->status, ST_TIMEOUT); ok = 0; break; }
+        if ((*(volatile int*)&ctrl->status & ST_TIMEOUT) || global_ns() > end) {
+          atomicOr(&ctrl->status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
       }
     }
     __threadfence();

@@ -122,7 +122,7 @@ struct mps_state {
                                  double rank_tol, void* U, double* S, void* V, void* Aq, void* Ap, double* out4) = 0;
   virtual mps_status tsvd_backward_device(int m, int n, int k, const void* U, const double* S, const void* V,
                                           const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) = 0;
-  virtual mps_status selftest_wait(long long spins) = 0;
+  virtual mps_status selftest_timeout(int site, long long wait_ns) = 0;
   int N = 0;
   int d = 2;
   int centre = 0;
@@ -924,16 +924,68 @@ struct Engine final : mps_state {
     return read_ctrl();
   }
 
-  // failure detection: a bounded wait on a word that nothing sets (the selection output slot 6,
-  // zeroed here) gives up, and the status word carries the timeout to the host
-  mps_status selftest_wait(long long spins) override {
+  // failure detection: a bounded wait whose signal never comes gives up at the handle's deadline,
+  // and the status word carries the timeout to the host (see mps_selftest_timeout)
+  mps_status selftest_timeout(int site, long long wait_ns) override {
     if (sticky) return from_bits(sticky);
-    if (spins < 1 || spins > (1LL << 31)) return MPS_ERR_ARG;
-    unsigned* flag = (unsigned*)((double*)outdev + 6);
+    if (site < MPS_SELFTEST_FLAG || site > MPS_SELFTEST_GEMM || wait_ns < 1000 || wait_ns > 20000000000LL)
+      return MPS_ERR_ARG;
+    if (site != MPS_SELFTEST_FLAG && !std::is_same<R, float>::value) return MPS_ERR_ARG;
+    if (site == MPS_SELFTEST_GEMM && !tc) return MPS_ERR_ARG;
     mps_status s;
-    if ((s = cu(cudaMemsetAsync(flag, 0, sizeof(unsigned), stream)))) return s;
-    if ((s = kl(wait_probe(flag, 1u, spins, ctrl, stream)))) return s;
-    return read_ctrl();
+    // the limit and the knob go to the device control block; mps_reset restores both
+    hctrl->wait_ns = (unsigned long long)wait_ns;
+    hctrl->test_fault = site;
+    if ((s = cu(cudaMemcpyAsync(&ctrl->wait_ns, &hctrl->wait_ns, sizeof(hctrl->wait_ns), cudaMemcpyHostToDevice,
+                                stream))))
+      return s;
+    if ((s = cu(cudaMemcpyAsync(&ctrl->test_fault, &hctrl->test_fault, sizeof(int), cudaMemcpyHostToDevice,
+                                stream))))
+      return s;
+    if (site == MPS_SELFTEST_FLAG) {
+      unsigned* flag = (unsigned*)((double*)outdev + 6);   // the selection output slot 6, zeroed here
+      if ((s = cu(cudaMemsetAsync(flag, 0, sizeof(unsigned), stream)))) return s;
+      if ((s = kl(wait_probe(flag, 1u, ctrl, stream)))) return s;
+      return read_ctrl();
+    }
+    if constexpr (std::is_same<R, float>::value) {
+      // a small problem of the kernel under test, on buffers of its own (zero data: the exchange
+      // protocol runs in every round whatever the values)
+      const int l = 64, c = (site == MPS_SELFTEST_JACOBI) ? 288 : 128;
+      float2 *x = nullptr, *xb = nullptr, *bb = nullptr, *cb = nullptr;
+      unsigned* fl = nullptr;
+      const size_t xcap = (size_t)1 << 21;
+      auto release = [&]() {
+        cudaStreamSynchronize(stream);
+        for (void* b : {(void*)x, (void*)xb, (void*)bb, (void*)cb, (void*)fl}) if (b) cudaFree(b);
+      };
+      if (cudaMalloc(&x, sizeof(float2) * l * c) != cudaSuccess || cudaMalloc(&xb, sizeof(float2) * xcap) != cudaSuccess ||
+          cudaMalloc(&bb, sizeof(float2) * 128 * 128) != cudaSuccess ||
+          cudaMalloc(&cb, sizeof(float2) * 128 * 128) != cudaSuccess || cudaMalloc(&fl, sizeof(unsigned) * 4096) != cudaSuccess) {
+        release();
+        return MPS_ERR_OOM;
+      }
+      s = cu(cudaMemsetAsync(x, 0, sizeof(float2) * l * c, stream));
+      if (!s) s = cu(cudaMemsetAsync(bb, 0, sizeof(float2) * 128 * 128, stream));
+      if (!s && site == MPS_SELFTEST_GEMM) {
+        s = cu(tc_gemm_selftest(tc, 128, 128, 64, x, bb, cb, stream, &ctrl->status, (unsigned long long)wait_ns));
+        ++n_launch;
+      } else if (!s) {
+        JacobiPlan plan = jacobi_plan<R>(l, c, false, sm_count, sm_count,
+                                         site == MPS_SELFTEST_GRAM ? MPS_SVD_GRAM : MPS_SVD_TOURNAMENT);
+        const bool right_kind = (site == MPS_SELFTEST_GRAM) ? plan.gram_R > 0 : (plan.gram_R == 0 && plan.cluster == 0 &&
+                                                                                  plan.nb / 2 > 1);
+        if (!right_kind) {
+          release();
+          return MPS_ERR_ARG;
+        }
+        s = kl(jacobi_launch<R>(plan, x, l, l, c, nullptr, 0, 4, ctrl, xb, xcap, fl, 4096, stream));
+      }
+      mps_status r = s ? s : read_ctrl();
+      release();
+      return r;
+    }
+    return MPS_ERR_ARG;
   }
 
   mps_status fidelity(double* out) override {
@@ -1473,9 +1525,9 @@ mps_status mps_tsvd_backward_device(mps_handle h, int m, int n, int k, const voi
   return h->tsvd_backward_device(m, n, k, U, S, V, Aq_bar, Ap_bar, eps, A_bar);
 }
 
-mps_status mps_selftest_wait(mps_handle h, long long spins) {
+mps_status mps_selftest_timeout(mps_handle h, int site, long long wait_ns) {
   if (!h) return MPS_ERR_ARG;
-  return h->selftest_wait(spins);
+  return h->selftest_timeout(site, wait_ns);
 }
 
 mps_status mps_fidelity(mps_handle h, double* inferred) {

@@ -41,7 +41,6 @@ constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * BKR * 4;          // 16 KB, same for A and B tiles (BN == BM)
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr long long kWaitLimit = 40000000LL;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -63,10 +62,12 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait on an mbarrier phase; on timeout sets ST_TIMEOUT and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, unsigned long long wait_ns) {
+  const unsigned long long end = global_ns() + wait_ns;
+  for (int i = 0;; ++i) {
     if (mbar_test(bar, parity)) return true;
     if (i > 64) __nanosleep(20);
+    if (global_ns() > end) break;
   }
   atomicOr(status, ST_TIMEOUT);
   return false;
@@ -130,11 +131,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Bounded wait that also gives up as soon as another role of the CTA aborted.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, int* status,
-                                                   volatile int* abort_flag) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
+                                                   volatile int* abort_flag, unsigned long long wait_ns) {
+  const unsigned long long end = global_ns() + wait_ns;
+  for (int i = 0;; ++i) {
     if (mbar_test(bar, parity)) return true;
     if ((i & 255) == 255 && *abort_flag) return false;
     if (i > 64) __nanosleep(20);
+    if (global_ns() > end) break;
   }
   atomicOr(status, ST_TIMEOUT);
   *abort_flag = 1;
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap mBl,
                                                               int M, int N, int nkb, float alpha,
                                                               float2* __restrict__ C, long long c_rs, long long c_cs,
-                                                              int* status) {
+                                                              int* status, int fault, unsigned long long wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -185,11 +188,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer
+      // ---------------- TMA producer (failure self-test: CTA (0, 0) issues nothing, so that its
+      // MMA issuer's wait on the first stage runs out)
       int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
+      const int nload = (fault && blockIdx.x == 0 && blockIdx.y == 0) ? 0 : nkb;
+      for (int kb = 0; kb < nload; ++kb) {
         const int s = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait_or_abort(&empty_bar[s], ((kb / STAGES) - 1) & 1, status, abortp)) break;
+        if (kb >= STAGES && !mbar_wait_or_abort(&empty_bar[s], ((kb / STAGES) - 1) & 1, status, abortp, wait_ns)) break;
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full_bar[s], STAGE_BYTES);
         tma_load_2d(st + 0 * TILE_BYTES, &mAh, &full_bar[s], kb * BKR, m0);
@@ -200,15 +205,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       }
       // every issued copy must land before the CTA may exit
       for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, status);
+        mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, status, wait_ns);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer: one K block per accumulator, buffers alternate
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, b = kb & 1;
-        if (!mbar_wait_or_abort(&full_bar[s], (kb / STAGES) & 1, status, abortp)) break;
-        if (kb >= 2 && !mbar_wait_or_abort(&acc_empty[b], ((kb >> 1) - 1) & 1, status, abortp)) break;
+        if (!mbar_wait_or_abort(&full_bar[s], (kb / STAGES) & 1, status, abortp, wait_ns)) break;
+        if (kb >= 2 && !mbar_wait_or_abort(&acc_empty[b], ((kb >> 1) - 1) & 1, status, abortp, wait_ns)) break;
         tc_fence_after();
         const uint32_t base = su32(smem + s * STAGE_BYTES);
         const uint64_t dAh = sdesc(base), dAl = sdesc(base + TILE_BYTES);
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       const int b = kb & 1;
-      if (!mbar_wait_or_abort(&acc_full[b], (kb >> 1) & 1, status, abortp)) { ok = false; break; }
+      if (!mbar_wait_or_abort(&acc_full[b], (kb >> 1) & 1, status, abortp, wait_ns)) { ok = false; break; }
       tc_fence_after();
 #pragma unroll
       for (int ch = 0; ch < BN / 32; ++ch) {
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   }
   __syncthreads();
   // no MMA may still write TMEM when it is released
-  mbar_wait(&done_bar, 0, status);
+  mbar_wait(&done_bar, 0, status, wait_ns);
   tc_fence_after();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
@@ -387,7 +392,7 @@ namespace {
 cudaError_t tc_gemm_on(float* ah, float* al, float* bh, float* bl, int M, int N, int K, float alpha, const float2* A,
                        long long a_rs, long long a_cs, int conjA, const float2* B, long long b_rs, long long b_cs,
                        int conjB, float2* C, long long c_rs, long long c_cs, cudaStream_t st, int* launched,
-                       int* status) {
+                       int* status, int fault = 0, unsigned long long wait_ns = kWaitNs) {
   *launched = 0;
   const int kpad = ((2 * K + BKR - 1) / BKR) * BKR;
   pack_a_kernel<<<grid_for((long long)M * kpad / 2), 256, 0, st>>>(A, a_rs, a_cs, conjA, M, K, kpad, ah, al);
@@ -400,7 +405,7 @@ cudaError_t tc_gemm_on(float* ah, float* al, float* bh, float* bl, int M, int N,
     return cudaErrorInvalidValue;
   dim3 grid((2 * N + BN - 1) / BN, (M + BM - 1) / BM);
   tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, kpad / BKR, alpha, C, c_rs, c_cs,
-                                                     status);
+                                                     status, fault, wait_ns);
   *launched = 3;
   return cudaGetLastError();
 }
@@ -413,6 +418,14 @@ cudaError_t tc_gemm_raw(float* ah, float* al, float* bh, float* bl, int M, int N
                         int* launched, int* status) {
   return tc_gemm_on(ah, al, bh, bl, M, N, K, alpha, A, a_rs, a_cs, conjA, B, b_rs, b_cs, conjB, C, c_rs, c_cs, st,
                     launched, status);
+}
+
+cudaError_t tc_gemm_selftest(TcGemm* g, int M, int N, int K, const float2* A, const float2* B, float2* C,
+                             cudaStream_t st, int* status, unsigned long long wait_ns) {
+  if (!tc_fits(g, M, N, K) || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  int launched = 0;
+  return tc_gemm_on(g->ah, g->al, g->bh, g->bl, M, N, K, 1.f, A, K, 1, 0, B, N, 1, 0, C, N, 1, st, &launched, status,
+                    1, wait_ns);
 }
 
 const void* tc_gemm_kernel_entry() { return (const void*)tc_gemm_kernel; }
@@ -476,7 +489,7 @@ extern "C" mps_status mps_cgemm_c64_noalloc(int M, int N, int K, float alpha, co
   if (M < 0 || N < 0 || K < 0 || !A || !B || !C) return MPS_ERR_ARG;
   if (M == 0 || N == 0) return MPS_OK;
   if (K == 0) return MPS_ERR_ARG;
-  const size_t kpad = (size_t)((2 * K + 31) / 32) * 32;
+  const size_t kpad = (2 * (size_t)K + 31) / 32 * 32;   // 64-bit: no int overflow for large K
   if ((size_t)M * kpad > kNoAllocPackFloats || (size_t)2 * N * kpad > kNoAllocPackFloats) {
     std::fprintf(stderr,
                  "eamps: mps_cgemm_c64_noalloc: shape %d x %d x %d exceeds the fixed workspace "

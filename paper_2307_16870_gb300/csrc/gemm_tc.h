@@ -27,6 +27,11 @@ cudaError_t tc_gemm_raw(float* ah, float* al, float* bh, float* bl, int M, int N
                         const float2* A, long long a_rs, long long a_cs, int conjA, const float2* B, long long b_rs,
                         long long b_cs, int conjB, float2* C, long long c_rs, long long c_cs, cudaStream_t st,
                         int* launched, int* status);
+// Failure self-test: the same kernel with CTA (0, 0)'s loads withheld, so that its tensor-core
+// issuer's bounded wait (wait_ns) runs out: ST_TIMEOUT in *status, every role returns, the
+// tensor memory is released.  Row-major A (M x K), B (K x N), C (M x N).
+cudaError_t tc_gemm_selftest(TcGemm* g, int M, int N, int K, const float2* A, const float2* B, float2* C,
+                             cudaStream_t st, int* status, unsigned long long wait_ns);
 const void* tc_gemm_kernel_entry();
 int tc_gemm_smem_bytes();
 

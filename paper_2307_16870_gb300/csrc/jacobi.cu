@@ -150,15 +150,17 @@ __device__ __forceinline__ unsigned atom_add_release(unsigned* a, unsigned v) {
   return old;
 }
 
-// Thread 0 waits (bounded) until *a >= target; the whole CTA then proceeds.
+// Thread 0 waits until *a >= target, for at most the handle's wall-clock wait limit (or until
+// another wait of the handle has given up); the whole CTA then proceeds.
 __device__ __forceinline__ bool cta_wait_geq(const unsigned* a, unsigned target, DevCtrl* ctrl) {
   __shared__ int ok_s;
   if (threadIdx.x == 0) {
     int ok = 1;
-    long long spins = 0;
+    const unsigned long long end = wait_deadline(ctrl);
+    int polls = 0;
     while (ld_acquire(a) < target) {
-      if (++spins > 64) __nanosleep(20);
-      if (spins > kSpinLimit || (*(volatile int*)&ctrl->status & ST_TIMEOUT)) {
+      if (++polls > 64) __nanosleep(20);
+      if ((*(volatile int*)&ctrl->status & ST_TIMEOUT) || global_ns() > end) {
         atomicOr(&ctrl->status, ST_TIMEOUT);
         ok = 0;
         break;
@@ -170,12 +172,14 @@ __device__ __forceinline__ bool cta_wait_geq(const unsigned* a, unsigned target,
   return ok_s != 0;
 }
 
-// Thread 0 only: bounded spin until *a >= target (sets ST_TIMEOUT and returns false on expiry).
+// Thread 0 only: wait until *a >= target, bounded as cta_wait_geq (sets ST_TIMEOUT and returns
+// false on expiry).
 __device__ __forceinline__ bool spin_geq(const unsigned* a, unsigned target, DevCtrl* ctrl) {
-  long long spins = 0;
+  const unsigned long long end = wait_deadline(ctrl);
+  int polls = 0;
   while (ld_acquire(a) < target) {
-    if (++spins > 64) __nanosleep(20);
-    if (spins > kSpinLimit || (*(volatile int*)&ctrl->status & ST_TIMEOUT)) {
+    if (++polls > 64) __nanosleep(20);
+    if ((*(volatile int*)&ctrl->status & ST_TIMEOUT) || global_ns() > end) {
       atomicOr(&ctrl->status, ST_TIMEOUT);
       return false;
     }
@@ -197,9 +201,11 @@ __device__ __forceinline__ void xbar_expect(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void xbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
-// Bounded wait for the phase of the given parity; false on expiry.
-__device__ __forceinline__ bool xbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+// Wait for the phase of the given parity, bounded by the handle's wall-clock wait limit; false
+// on expiry.
+__device__ __forceinline__ bool xbar_wait(uint64_t* bar, uint32_t parity, const DevCtrl* ctrl) {
+  const unsigned long long end = wait_deadline(ctrl);
+  for (;;) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -207,8 +213,8 @@ __device__ __forceinline__ bool xbar_wait(uint64_t* bar, uint32_t parity) {
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
     if (done) return true;
+    if (global_ns() > end) return false;
   }
-  return false;
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -602,6 +608,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
   bool converged = false;
   int sweep = 0;
   unsigned rnd = 0;   // rounds completed over all sweeps
+  const bool withhold = cta == 0 && *(volatile const int*)&p.ctrl->test_fault == 1;
 
   // round 0 of the first sweep: position q holds player q
   for (int s = threadIdx.x; s < 2 * w; s += blockDim.x) {
@@ -620,23 +627,32 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
         // take the blocks that moved into my positions
         if (bulk) {
           if (threadIdx.x == 0) {
+            // both sources first: a copy is issued only once every source block is published,
+            // so a wait that gives up never leaves a copy in flight into this CTA
             int ok = 1;
             for (int h = 0; h < 2 && ok; ++h) {
               if (pos[h] == 0) continue;                  // block 0 never moves
               const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
-              if (!spin_geq(p.flags + src, rnd, p.ctrl)) { ok = 0; break; }
-              asm volatile("fence.proxy.async.global;" ::: "memory");
-              xbar_expect(&xbar, blk_bytes);
-              bulk_load(slots + h * blk, p.xch + ((long long)((rnd - 1) & 1) * nb + src) * blk, blk_bytes, &xbar);
+              if (!spin_geq(p.flags + src, rnd, p.ctrl)) ok = 0;
             }
-            xbar_arrive(&xbar);   // the phase completes when the issued copies have landed
+            if (ok) {
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              for (int h = 0; h < 2; ++h) {
+                if (pos[h] == 0) continue;
+                const int src = (pos[h] == nb - 1) ? 1 : pos[h] + 1;
+                xbar_expect(&xbar, blk_bytes);
+                bulk_load(slots + h * blk, p.xch + ((long long)((rnd - 1) & 1) * nb + src) * blk, blk_bytes, &xbar);
+              }
+            }
+            xbar_arrive(&xbar);   // the phase completes when the issued copies (if any) have landed
             xok_s = ok;
           }
-          const bool landed = xbar_wait(&xbar, xphase);
+          // every thread waits only for copies that were issued from published sources
+          const bool landed = xbar_wait(&xbar, xphase, p.ctrl);
           xphase ^= 1u;
           if (__syncthreads_or(!landed)) {
             if (threadIdx.x == 0) atomicOr(&p.ctrl->status, ST_TIMEOUT);
-            xbar_wait(&xbar, xphase ^ 1u);   // let copies in flight land before the CTA exits
+            xbar_wait(&xbar, xphase ^ 1u, p.ctrl);   // one more bounded wait for them to land
             return;
           }
           if (!xok_s) return;
@@ -664,7 +680,9 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
       // shared-memory writes above must be visible to the bulk stores below
       if (bulk) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      if (P > 1) {
+      // failure self-test: CTA 0 withholds its publications (a later one would also satisfy a
+      // wait for an earlier round), so its neighbours' waits run out
+      if (P > 1 && !withhold) {
         // publish both blocks of this round (block 0 stays in CTA 0)
         float2* to = p.xch + (long long)(rnd & 1) * nb * blk;
         if (bulk) {

@@ -209,6 +209,8 @@ __global__ void __launch_bounds__(kThreads) jacobi_gram_kernel(GArgs p) {
   }
 
   int my_rot = 0, my_big = 0;   // rotations decided by this thread, those above tol_stop
+  // failure self-test: slot 0's first CTA withholds its releases, so its neighbour's wait runs out
+  const bool withhold = blockIdx.x == 0 && *(volatile const int*)&p.ctrl->test_fault == 2;
   int local_abort = 0;
   unsigned long long rot_total = 0;
   bool converged = false, aborted = false;
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_gram_kernel(GArgs p) {
         __syncthreads();
         if (tid == 0) {
           __threadfence();
-          st_release_u32(fl + (slot * 2 + dir) * R + rank, gr + 1);
+          if (!withhold) st_release_u32(fl + (slot * 2 + dir) * R + rank, gr + 1);
           int ok = 1;
           if (!local_abort) ok = wait_geq(fl + (from * 2 + dir) * R + rank, gr + 1, p.ctrl);
           ok_s = ok && !local_abort;

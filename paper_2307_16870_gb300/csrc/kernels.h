@@ -193,9 +193,9 @@ cudaError_t tsvd_scale(cplx<R>* Y, int rows, int c, int k, const double* s, cuda
 template <class R>
 cudaError_t tsvd_core(int c, const cplx<R>* Ju, const cplx<R>* Jv, const double* s, const double* sbar, double eps,
                       const cplx<R>* Zc, int zc_adjoint, cplx<R>* G, cudaStream_t st);
-// Bounded wait of one thread for *flag >= target; ST_TIMEOUT in ctrl->status after `limit`
-// iterations (selftest.cu).
-cudaError_t wait_probe(const unsigned* flag, unsigned target, long long limit, DevCtrl* ctrl, cudaStream_t st);
+// Wait of one thread for *flag >= target, bounded by ctrl->wait_ns; ST_TIMEOUT in ctrl->status
+// on expiry (selftest.cu).
+cudaError_t wait_probe(const unsigned* flag, unsigned target, DevCtrl* ctrl, cudaStream_t st);
 // dst (rows x cols, ld ldd) += op(src) with src(r, j) at src + r * s_rs + j * s_cs.
 template <class R>
 cudaError_t cadd_strided(cplx<R>* dst, long long ldd, int rows, int cols, const cplx<R>* src, long long s_rs,

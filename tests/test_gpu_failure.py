@@ -1,6 +1,10 @@
-"""Failure detection without a GPU fault: a bounded device wait on a flag that nothing sets runs
-out, the kernel records the timeout in the status word and returns, the host reads the error,
-the handle stays failed (sticky) until mps_reset, and the context stays usable."""
+"""Failure detection without a GPU fault: a signal is withheld, the bounded wait for it runs out
+at the handle's wall-clock limit, the kernel records the timeout in the status word and every
+CTA returns; the host reads the error, the handle stays failed (sticky) until mps_reset, the
+context stays usable and other handles are unaffected.  The waits tested are the real ones: a
+single-flag wait, the block exchange of the point-to-point Jacobi kernel, the exchange and
+cluster agreement of the Gram-matrix block Jacobi kernel, and the mbarrier pipeline of the
+tensor-core contraction."""
 import time
 
 import numpy as np
@@ -14,17 +18,20 @@ E = pytest.importorskip("paper_2307_16870_gb300")
 import workloads as W  # noqa: E402
 from oracle import statevector as SV  # noqa: E402
 
+SITES = ["flag", "jacobi", "gram", "gemm"]
 
-def test_a_wait_that_runs_out_is_reported_and_the_handle_recovers_after_reset():
+
+@pytest.mark.parametrize("site", range(4), ids=SITES)
+def test_a_wait_that_runs_out_is_reported_and_the_handle_recovers_after_reset(site):
     n = 6
-    m = E.MPS(n)
+    m = E.MPS(n, precision=E.TF32X3)
     u = W.haar_unitary(4, 3, 0)
     m.apply_2q(2, u)
     t0 = time.perf_counter()
     with pytest.raises(E.MpsError) as ei:
-        E.mps_selftest_wait(m.h, 1000000)
+        E.mps_selftest_timeout(m.h, site, 50_000_000)   # 50 ms limit
     assert ei.value.code == 8                      # MPS_ERR_TIMEOUT
-    assert time.perf_counter() - t0 < 10.0
+    assert time.perf_counter() - t0 < 5.0          # every CTA returned promptly
     with pytest.raises(E.MpsError):                # sticky until reset
         m.apply_2q(0, u)
     m.reset()
@@ -38,6 +45,13 @@ def test_a_wait_that_runs_out_is_reported_and_the_handle_recovers_after_reset():
     other.apply_2q(1, u)
     assert abs(other.fidelity() - 1.0) < 1e-12
     other.close()
-    with pytest.raises(E.MpsError):
-        E.mps_selftest_wait(m.h, 0)                # out of range
+    m.close()
+
+
+def test_self_test_arguments():
+    m = E.MPS(4, precision=E.FP64)
+    for site, ns in [(4, 10**6), (-1, 10**6), (0, 10), (0, 10**12), (1, 10**6), (3, 10**6)]:
+        with pytest.raises(E.MpsError) as ei:      # out of range, or a complex64 site on an FP64 handle
+            E.mps_selftest_timeout(m.h, site, ns)
+        assert ei.value.code == 1
     m.close()
