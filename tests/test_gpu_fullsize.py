@@ -77,3 +77,50 @@ def test_single_update_mpo_exact_input(name, prec, tol):
     rel = np.abs(s_gpu[:k] - rec["s"][:k]) / rec["s"][:k]
     assert rel.max() < tol, rel.max()
     assert abs(m.lognorm() - orc.lognorm) < 1e-6
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS[:2])
+@pytest.mark.parametrize("centre", [12, 10])
+def test_single_update_theta_1024_pure_chi_512(name, prec, tol, centre):
+    """The largest point of the pure-state benchmark (fixed chi = 512): bonds 512 around the pair,
+    theta 1024 x 1024 (the Gram-matrix block Jacobi layout), with and without centre moves."""
+    n, cap, q = 24, 512, 12
+    sites, _ = random_canonical_mps(n, cap, centre, seed=610 + centre)
+    u = W.haar_unitary(4, 611, q)
+    orc = _oracle_from(sites, centre, cap=cap)
+    rec = orc.apply_2q(q, u, target=0.999)
+    m = E.MPS(n, chi_max=cap, precision=prec)
+    m.load_sites(sites, centre)
+    m.apply_2q(q, u, 0.999)
+    g = m.truncation_log()[-1]
+    assert g["rank_bound"] == rec["rank_bound"] == 1024
+    assert g["k"] == rec["k"], (g["k"], rec["k"])
+    k = rec["k"]
+    rel = np.abs(m.last_singular_values()[:k] - rec["s"][:k]) / rec["s"][:k]
+    assert rel.max() < tol, rel.max()
+    assert abs(g["f"] - rec["f"]) < tol
+    assert m.bond_dims() == orc.bond_dims()
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS[:2])
+def test_single_update_mpo_cap_256_theta_1024(name, prec, tol):
+    """Mixed state at its full size: d = 4 sites with bonds capped at 256, theta 1024 x 1024, a
+    noisy superoperator (gate, two-qubit depolarising, amplitude damping on both qubits)."""
+    from oracle import superop as SO
+    n, cap, centre, q = 12, 256, 6, 6
+    sites, _ = random_canonical_mps(n, cap, centre, seed=779, d=4)
+    ad = W.amplitude_damping_kraus(0.005)
+    s_op = np.kron(SO.from_kraus(ad, 1), SO.from_kraus(ad, 1)) @ \
+        SO.from_kraus(W.depolarizing_2q_kraus(0.01), 2) @ SO.from_unitary(W.haar_unitary(4, 780, 0))
+    orc = _oracle_from(sites, centre, kind=T.MIXED, cap=cap)
+    rec = orc.apply_2q(q, s_op, target=0.95)
+    m = E.MPS(n, kind=E.MIXED, chi_max=cap, precision=prec)
+    m.load_sites(sites, centre)
+    m.apply_2q(q, s_op, 0.95)
+    g = m.truncation_log()[-1]
+    assert g["rank_bound"] == rec["rank_bound"] == 1024
+    assert g["k"] == rec["k"]
+    k = rec["k"]
+    rel = np.abs(m.last_singular_values()[:k] - rec["s"][:k]) / rec["s"][:k]
+    assert rel.max() < tol, rel.max()
+    assert abs(m.lognorm() - orc.lognorm) < 1e-6
