@@ -60,6 +60,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-sample-s", type=float, default=20.0, help="seconds of oracle work per CPU sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-target, chi = 512 and precision blocks of the bench line")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies", "grad", "vidal", "precision"],
                     help="ttf: time to target fidelity, EA against fixed bond dimensions; "
@@ -76,6 +78,14 @@ def parse_args(argv=None):
                     help="instead of the circuit: a few two-site updates on a random canonical 24-site MPS "
                          "with every bond CHI (the launch configuration of the circuit's saturated gates)")
     return ap.parse_args(argv)
+
+
+def bench_config(a, n_2q: int, world: int) -> dict:
+    """The workload keys both arms print (the GPU arm and the oracle arm measure the same circuit)."""
+    return {"workload": workload_name(a), "n_qubits": a.n_qubits, "depth": a.depth, "n_2q": n_2q, "seed": a.seed,
+            "chi_cap": a.chi_cap, "f_min": a.f_min, "fixed_chi": a.fixed_chi, "strategy": "global",
+            "l2": f"GPU arm: flushed between timed steps ({a.flush_mb} MB write); CPU arm: not applicable",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def workload_name(a) -> str:
@@ -203,7 +213,7 @@ def run_reference(a) -> int:
     line = {"impl": "reference", "metric": "2-qubit MPS updates/s", "value": value, "unit": "updates/s",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "n_qubits": a.n_qubits, "depth": a.depth, "seed": a.seed},
+            "precision": "fp64", "config": bench_config(a, circ.n_2q, 1),
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": samples[-1]["cores"], "kind": "oracle",
                              "sample": samples[-1]["sample"]},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -212,6 +222,22 @@ def run_reference(a) -> int:
 
 
 # ------------------------------------------------------------------ GPU arm
+# DRAM traffic of one theta 512 x 512 launch of the point-to-point Jacobi kernel, from the ncu
+# capture named here (re-taken whenever that kernel changes; None when no capture of the current
+# kernel exists)
+TRAFFIC_512 = None
+TRAFFIC_SOURCE = "no ncu capture of the current kernel (traffic not measured by this run)"
+
+
+def measured_peaks() -> dict:
+    """The generated peaks of this GPU pool (HBM copy GB/s, bf16 TFLOP/s), if present."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
     # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -302,15 +328,18 @@ def run_ours(a) -> int:
     peak = fp32_peak_tflops(sm_count, 2070.0) if a.precision != "fp64" else None
     jac_s = st["jacobi_ms"] / 1e3
     achieved = (st["jacobi_flops"] / jac_s / 1e12) if jac_s > 0 else None
-    # DRAM bytes of one 512 x 512 launch of the point-to-point kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum of an ncu capture of the current kernel); the algorithmic bytes of
-    # that launch are one read and one write of theta, 2 x 512 x 512 x 8 B
-    traffic_512 = 2141184 + 31744
+    # DRAM bytes of one 512 x 512 launch of the point-to-point kernel: dram__bytes_read.sum +
+    # dram__bytes_write.sum of the ncu capture summarised in TRAFFIC_SOURCE (not measured by this
+    # run); the algorithmic bytes of that launch are one read and one write of theta,
+    # 2 x 512 x 512 x 8 B
+    peaks = measured_peaks()
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) / 2.0   # the tf32 rate is half the bf16 rate
     roof = {"bound": "alu", "kernel": "jacobi_kernel3 and the other one-sided Jacobi SVD kernels, FP32",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if (achieved and peak) else None,
-            "traffic": traffic_512 if a.precision != "fp64" else None,
+            "traffic": TRAFFIC_512 if a.precision != "fp64" else None,
             "traffic_launch": "jacobi_kernel3, theta 512 x 512 (bytes per launch; algorithmic 4194304)",
+            "traffic_source": TRAFFIC_SOURCE,
             "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, not measured)",
             "share_of_step": (st["jacobi_ms"] / sum(step_ms)) if step_ms else None,
             "launches": st["jacobi_launches"], "avg_launch_ms": st["jacobi_ms"] / max(st["jacobi_launches"], 1),
@@ -318,8 +347,19 @@ def run_ours(a) -> int:
             "centre_move_share": (st["move_jacobi_ms"] / st["jacobi_ms"]) if st["jacobi_ms"] else None}
     qr = {"launches": st["qr_launches"], "ms": st["qr_ms"],
           "share_of_step": (st["qr_ms"] / sum(step_ms)) if step_ms else None}
-    gemm = {"launches": st["gemm_launches"], "ms": st["gemm_ms"],
-            "tflops": (st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12) if st["gemm_ms"] > 0 else None}
+    gemm_tf = (st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12) if st["gemm_ms"] > 0 else None
+    gemm = {"launches": st["gemm_launches"], "ms": st["gemm_ms"], "tflops": gemm_tf,
+            "issued_tensor_tflops": 3 * gemm_tf if gemm_tf else None,
+            "tensor_peak_tflops": tf32_peak,
+            "tensor_peak_source": "tf32 = bf16 burst of the measured peaks / 2 (nominal ratio)"
+                                  if "bf16_tflops" in peaks else "tf32 = fallback 1.9 PFLOP/s bf16 / 2"}
+    # the contraction's share of the tensor pipe: 3xTF32 issues three products per useful one
+    roof["contraction_frac"] = (3 * gemm_tf / tf32_peak) if gemm_tf else None
+    extras = {}
+    if rank == 0 and world == 1 and not a.no_extras:
+        extras["time_to_target"] = time_to_target(E, torch, dev, a, prec)
+        extras["chi512"] = chi512_throughput(E, torch, dev, a, prec, circ, ops_dev, qs)
+        extras["precision_vs_fp64"] = precision_vs_fp64(E, a, prec, circ)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_oracle_sample(circ, a, a.cpu_sample_s)
@@ -328,15 +368,12 @@ def run_ours(a) -> int:
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(step_ms),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if a.precision == "fp64" else "f32",
-                "data": "synthetic",
-                "config": {"workload": workload_name(a), "n_qubits": a.n_qubits, "depth": a.depth,
-                           "n_2q": n, "seed": a.seed, "precision": a.precision, "chi_cap": a.chi_cap,
-                           "f_min": a.f_min, "fixed_chi": a.fixed_chi,
-                           "l2": f"flushed between timed steps ({a.flush_mb} MB write)",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                "data": "synthetic", "precision": a.precision,
+                "config": bench_config(a, n, world),
                 "inferred_fidelity": fid, "final_max_bond": max(bonds),
                 "wall_s_timed": wall, "gpu_launches": st["kernel_launches"], "roofline": roof,
                 "contraction": gemm, "householder_qr": qr, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     m.close()
     if world > 1:
@@ -362,6 +399,73 @@ def _timed_circuit(E, torch, dev, n_qubits, qs, ops_dev, op_dim, **mps_kw):
     st = m.stats()
     out = (e0.elapsed_time(e1), fid, max(m.bond_dims()), st["jacobi_ms"], st["jacobi_launches"])
     m.close()
+    return out
+
+
+def time_to_target(E, torch, dev, a, prec) -> dict:
+    """The paper's time-to-fidelity comparison ("Benchmarks"): an EA run at F_min on a circuit where
+    the fidelity budget binds (the same 100-qubit chain, brickwork depth 8, same seed), then a
+    fixed-bond run at the largest bond the EA run used.  Median GPU time of three runs each."""
+    circ = W.brickwork_circuit(a.n_qubits, 8, a.seed)
+    n = circ.n_2q
+    ops_dev = torch.from_numpy(circ.ops_array().view(np.float64).reshape(n, 32).copy()).to(dev)
+    qs = np.asarray(circ.qs, dtype=np.int32)
+    kw = dict(precision=prec, svd_kernel=svd_kernel_of(a, E))
+    ea = [_timed_circuit(E, torch, dev, a.n_qubits, qs, ops_dev, 4, f_min=a.f_min, n_2q=n, strategy=E.GLOBAL,
+                         chi_max=a.chi_cap, **kw) for _ in range(3)]
+    chi = ea[0][2]
+    fx = [_timed_circuit(E, torch, dev, a.n_qubits, qs, ops_dev, 4, n_2q=n, fixed_chi=chi, chi_max=chi, **kw)
+          for _ in range(3)]
+    ea_s = statistics.median(r[0] for r in ea) / 1e3
+    fx_s = statistics.median(r[0] for r in fx) / 1e3
+    return {"workload": f"{a.n_qubits}-qubit chain, brickwork depth 8, Haar SU(4), seed {a.seed}, {n} gates",
+            "f_min": a.f_min,
+            "ea": {"gpu_s": ea_s, "inferred_fidelity": ea[0][1], "max_bond": chi,
+                   "reached_f_min": bool(ea[0][1] >= a.f_min)},
+            "fixed_chi": {"chi": chi, "gpu_s": fx_s, "inferred_fidelity": fx[0][1]},
+            "ea_time_over_fixed": ea_s / fx_s}
+
+
+def chi512_throughput(E, torch, dev, a, prec, circ, ops_dev, qs) -> dict:
+    """Fixed bond 512 (the largest fixed-chi point of the pure-state benchmark) on the same circuit:
+    every saturated update is a 1024 x 1024 SVD."""
+    n = circ.n_2q
+    ms, fid, mx, jms, jl = _timed_circuit(E, torch, dev, a.n_qubits, qs, ops_dev, 4, n_2q=n, fixed_chi=512,
+                                          chi_max=512, precision=prec, svd_kernel=svd_kernel_of(a, E))
+    return {"workload": f"same circuit, fixed chi = 512 ({n} gates)", "updates_per_s": n / (ms / 1e3),
+            "gpu_s": ms / 1e3, "inferred_fidelity": fid, "max_bond": mx, "jacobi_share": jms / ms,
+            "jacobi_ms_per_launch": jms / max(jl, 1)}
+
+
+def precision_vs_fp64(E, a, prec, circ, n_prefix: int = 350) -> dict:
+    """The complex64 path against the complex128 path on the GPU (MPS_FP64), on the first n_prefix
+    gates of the benchmark circuit with the benchmark's schedule: the largest relative error of
+    the retained singular values per gate, of the running product, and the overlap of the states."""
+    n_prefix = min(n_prefix, circ.n_2q)
+    runs = {}
+    for name, pr in (("fp64", E.FP64), ("ours", prec)):
+        m = E.MPS(a.n_qubits, f_min=a.f_min, n_2q=circ.n_2q, strategy=E.GLOBAL, chi_max=a.chi_cap, precision=pr,
+                  svd_kernel=svd_kernel_of(a, E))
+        sv = []
+        for g in range(n_prefix):
+            q, u = circ.gates()[g]
+            m.apply_2q(q, u)
+            sv.append(m.last_singular_values())
+        runs[name] = (m, m.truncation_log(), sv)
+    (m64, log64, sv64), (m32, log32, sv32) = runs["fp64"], runs["ours"]
+    compared, rel = 0, 0.0
+    for g64, g32, s64, s32 in zip(log64, log32, sv64, sv32):
+        if g64["k"] != g32["k"]:
+            break
+        k = g64["k"]
+        rel = max(rel, float(np.max(np.abs(s32[:k] - s64[:k]) / s64[:k])))
+        compared += 1
+    out = {"gates": n_prefix, "gates_with_equal_bonds": compared, "max_bond": max(m64.bond_dims()),
+           "max_rel_err_retained_s": rel, "product_fp64": m64.fidelity(), "product_ours": m32.fidelity(),
+           "abs_err_product": abs(m64.fidelity() - m32.fidelity()),
+           "overlap_with_fp64": abs(m64.overlap(m32)) ** 2}
+    m64.close()
+    m32.close()
     return out
 
 
