@@ -21,6 +21,7 @@
 // relative, measured); summing one K block at a time on the CUDA cores keeps
 // the product at FP32 accuracy.  Every mbarrier wait is bounded; a timeout
 // sets the status bit and the CTA drains its copies and MMAs and returns.
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -41,6 +42,8 @@ constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * BKR * 4;          // 16 KB, same for A and B tiles (BN == BM)
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int kMaxSplit = 4;          // split-K factor limit
+constexpr int kSplitTarget = 128;     // CTAs a split-K launch aims for (152 SMs)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -151,9 +154,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap mAl,
                                                               const __grid_constant__ CUtensorMap mBh,
                                                               const __grid_constant__ CUtensorMap mBl,
-                                                              int M, int N, int nkb, float alpha,
+                                                              int M, int N, int nkb, int kb_per, float alpha,
                                                               float2* __restrict__ C, long long c_rs, long long c_cs,
-                                                              int* status, int fault, unsigned long long wait_ns) {
+                                                              int nsplit, int* status, int fault,
+                                                              unsigned long long wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -166,6 +170,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM;
   const int n0 = blockIdx.x * BN;   // real columns of D
+  // split K (nsplit > 1): the CTAs of a cluster along z take K blocks [kb0, kb0 + nloc) each and
+  // sum their partial products through distributed shared memory in z order (deterministic)
+  const int kb0 = blockIdx.z * kb_per;
+  const int nloc = min(kb_per, nkb - kb0);
   volatile int* abortp = &abort_s;
 
   if (threadIdx.x == 0) {
@@ -191,16 +199,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       // ---------------- TMA producer (failure self-test: CTA (0, 0) issues nothing, so that its
       // MMA issuer's wait on the first stage runs out)
       int issued = 0;
-      const int nload = (fault && blockIdx.x == 0 && blockIdx.y == 0) ? 0 : nkb;
+      const int nload = (fault && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) ? 0 : nloc;
       for (int kb = 0; kb < nload; ++kb) {
         const int s = kb % STAGES;
         if (kb >= STAGES && !mbar_wait_or_abort(&empty_bar[s], ((kb / STAGES) - 1) & 1, status, abortp, wait_ns)) break;
         unsigned char* st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-        tma_load_2d(st + 0 * TILE_BYTES, &mAh, &full_bar[s], kb * BKR, m0);
-        tma_load_2d(st + 1 * TILE_BYTES, &mAl, &full_bar[s], kb * BKR, m0);
-        tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full_bar[s], kb * BKR, n0);
-        tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full_bar[s], kb * BKR, n0);
+        const int kx = (kb0 + kb) * BKR;
+        tma_load_2d(st + 0 * TILE_BYTES, &mAh, &full_bar[s], kx, m0);
+        tma_load_2d(st + 1 * TILE_BYTES, &mAl, &full_bar[s], kx, m0);
+        tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full_bar[s], kx, n0);
+        tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full_bar[s], kx, n0);
         issued = kb + 1;
       }
       // every issued copy must land before the CTA may exit
@@ -210,7 +219,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer: one K block per accumulator, buffers alternate
-      for (int kb = 0; kb < nkb; ++kb) {
+      for (int kb = 0; kb < nloc; ++kb) {
         const int s = kb % STAGES, b = kb & 1;
         if (!mbar_wait_or_abort(&full_bar[s], (kb / STAGES) & 1, status, abortp, wait_ns)) break;
         if (kb >= 2 && !mbar_wait_or_abort(&acc_empty[b], ((kb >> 1) - 1) & 1, status, abortp, wait_ns)) break;
@@ -240,7 +249,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
 #pragma unroll
     for (int i = 0; i < BN; ++i) acc[i] = 0.f;
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
+    for (int kb = 0; kb < nloc; ++kb) {
       const int b = kb & 1;
       if (!mbar_wait_or_abort(&acc_full[b], (kb >> 1) & 1, status, abortp, wait_ns)) { ok = false; break; }
       tc_fence_after();
@@ -255,7 +264,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
-    if (ok && !*abortp) {
+    if (nsplit > 1) {
+      // the partial product to shared memory (the operand stages are free: every MMA and every
+      // load of this CTA has completed), column-major by epilogue thread
+      float* pbuf = reinterpret_cast<float*>(smem);
+      const int te = threadIdx.x - 64;
+#pragma unroll
+      for (int c = 0; c < BN; ++c) pbuf[c * 128 + te] = acc[c];
+    } else if (ok && !*abortp) {
       const int row = m0 + qd * 32 + lane;
       if (row < M) {
 #pragma unroll
@@ -272,6 +288,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     }
   }
   __syncthreads();
+  if (nsplit > 1) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();   // every partial product of the cluster is in shared memory
+    if (warp >= 2) {
+      // rank r sums columns [r, r + 1, ...) / nsplit of the tile over the cluster, in z order
+      const int te = threadIdx.x - 64, qd = warp & 3;
+      const int row = m0 + qd * 32 + lane;
+      const int rank = (int)cl.block_rank();
+      const float* src[kMaxSplit];
+#pragma unroll
+      for (int z = 0; z < kMaxSplit; ++z) src[z] = cl.map_shared_rank(reinterpret_cast<float*>(smem), z < nsplit ? z : 0);
+      const int per = (BN / 2 + nsplit - 1) / nsplit;   // complex columns per rank (nsplit need not divide)
+      if (row < M) {
+#pragma unroll 4
+        for (int c2 = 0; c2 < per; ++c2) {
+          const int c = min(rank * per + c2, BN / 2 - 1);
+          const int j = (rank * per + c2 < BN / 2) ? n0 / 2 + c : N;   // j = N: nothing to write
+          float v[kMaxSplit][2];
+#pragma unroll
+          for (int z = 0; z < kMaxSplit; ++z) {
+            v[z][0] = (z < nsplit) ? src[z][(2 * c) * 128 + te] : 0.f;
+            v[z][1] = (z < nsplit) ? src[z][(2 * c + 1) * 128 + te] : 0.f;
+          }
+          float sx = v[0][0], sy = v[0][1];
+#pragma unroll
+          for (int z = 1; z < kMaxSplit; ++z) {
+            if (z < nsplit) { sx += v[z][0]; sy += v[z][1]; }
+          }
+          if (j < N) C[(long long)row * c_rs + (long long)j * c_cs] = make_float2(alpha * sx, alpha * sy);
+        }
+      }
+    }
+    cl.sync();   // every partial has been read: no CTA leaves before
+  }
   // no MMA may still write TMEM when it is released
   mbar_wait(&done_bar, 0, status, wait_ns);
   tc_fence_after();
@@ -392,7 +443,7 @@ namespace {
 cudaError_t tc_gemm_on(float* ah, float* al, float* bh, float* bl, int M, int N, int K, float alpha, const float2* A,
                        long long a_rs, long long a_cs, int conjA, const float2* B, long long b_rs, long long b_cs,
                        int conjB, float2* C, long long c_rs, long long c_cs, cudaStream_t st, int* launched,
-                       int* status, int fault = 0, unsigned long long wait_ns = kWaitNs) {
+                       int* status, int fault = 0, unsigned long long wait_ns = kWaitNs, bool allow_split = false) {
   *launched = 0;
   const int kpad = ((2 * K + BKR - 1) / BKR) * BKR;
   pack_a_kernel<<<grid_for((long long)M * kpad / 2), 256, 0, st>>>(A, a_rs, a_cs, conjA, M, K, kpad, ah, al);
@@ -403,9 +454,35 @@ cudaError_t tc_gemm_on(float* ah, float* al, float* bh, float* bl, int M, int N,
   if (!make_map(&mAh, ah, M, kpad) || !make_map(&mAl, al, M, kpad) || !make_map(&mBh, bh, 2 * N, kpad) ||
       !make_map(&mBl, bl, 2 * N, kpad))
     return cudaErrorInvalidValue;
+  const int nkb = kpad / BKR;
   dim3 grid((2 * N + BN - 1) / BN, (M + BM - 1) / BM);
-  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, kpad / BKR, alpha, C, c_rs, c_cs,
-                                                     status, fault, wait_ns);
+  // split K over a cluster along z until the grid fills the GPU (at least two K blocks a CTA)
+  int split = 1;
+  while (allow_split && split < kMaxSplit && (int)(grid.x * grid.y) * split < kSplitTarget && nkb >= 4 * split)
+    split *= 2;
+  const int kb_per = (nkb + split - 1) / split;
+  split = (nkb + kb_per - 1) / kb_per;
+  grid.z = split;
+  if (split == 1) {
+    tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, M, N, nkb, kb_per, alpha, C, c_rs, c_cs,
+                                                       1, status, fault, wait_ns);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = split;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e2 = cudaLaunchKernelEx(&cfg, tc_gemm_kernel, mAh, mAl, mBh, mBl, M, N, nkb, kb_per, alpha, C, c_rs,
+                                        c_cs, split, status, fault, wait_ns);
+    if (e2 != cudaSuccess) return e2;
+  }
   *launched = 3;
   return cudaGetLastError();
 }
@@ -438,7 +515,7 @@ cudaError_t tc_gemm(TcGemm* g, int M, int N, int K, float alpha, const float2* A
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (!tc_fits(g, M, N, K) || K <= 0) return cudaErrorInvalidValue;
   return tc_gemm_on(g->ah, g->al, g->bh, g->bl, M, N, K, alpha, A, a_rs, a_cs, conjA, B, b_rs, b_cs, conjB, C, c_rs,
-                    c_cs, st, launched, status);
+                    c_cs, st, launched, status, 0, kWaitNs, true);
 }
 
 }  // namespace eamps
