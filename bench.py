@@ -63,7 +63,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the time-to-target, chi = 512 and precision blocks of the bench line")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
-    ap.add_argument("--study", default="", choices=["", "ttf", "mpo", "batch", "strategies", "grad", "vidal", "precision"],
+    ap.add_argument("--study", default="",
+                    choices=["", "ttf", "mpo", "batch", "strategies", "grad", "vidal", "precision", "e1"],
                     help="ttf: time to target fidelity, EA against fixed bond dimensions; "
                          "mpo: the noisy EA-MPO workload (d = 4); "
                          "batch: 64 independent circuits run concurrently; "
@@ -572,6 +573,57 @@ def run_study(a) -> int:
                       "exact_max_bond": max(exact.bond_dims())})
                 m.close()
         exact.close()
+    elif a.study == "e1":
+        # Fig. 1 rerun at 25 qubits, depth 20: naive / global / nearest schedules at F_min 0.9 and
+        # 0.5, and the bond-cap trade-off (global, F_min 0.9, caps 64..512).  The true fidelity
+        # |<exact|EA>|^2 takes the exact state from a dense state-vector evolution (2^25 complex128
+        # amplitudes, 512 MB on the GPU, PyTorch tensor operations: measurement only, not the
+        # library's path) and contracts it with the EA state's sites.
+        n_q, depth = 25, 20
+        circ = W.brickwork_circuit(n_q, depth, a.seed)
+        n = circ.n_2q
+        ops_dev = torch.from_numpy(circ.ops_array().view(np.float64).reshape(n, 32).copy()).to(dev)
+        qs = np.asarray(circ.qs, dtype=np.int32)
+        psi = torch.zeros(2 ** n_q, dtype=torch.complex128, device=dev)
+        psi[0] = 1.0
+        for q, u in circ.gates():
+            ut = torch.from_numpy(np.ascontiguousarray(u)).to(dev)
+            v = psi.view(2 ** q, 4, 2 ** (n_q - q - 2))
+            psi = torch.einsum("ab,ibj->iaj", ut, v).reshape(-1)
+        torch.cuda.synchronize(dev)
+
+        def true_fidelity(m):
+            # <exact|m>: contract conj(psi) site by site, left to right
+            t = psi.conj().view(1, 2, -1)                     # (chi=1, sigma, rest)
+            for i in range(n_q):
+                site = torch.from_numpy(m.site(i)).to(dev)     # (chi_l, 2, chi_r)
+                t = torch.einsum("lsr,lsk->rk", site, t)       # (chi_r, rest)
+                if i + 1 < n_q:
+                    t = t.reshape(t.shape[0], 2, -1)
+            return float(abs(t.reshape(-1)[0]) ** 2)
+
+        names = {E.NAIVE: "naive", E.GLOBAL: "global", E.NEAREST: "nearest"}
+        runs = [("strategy", f_min, strat, 512) for f_min in (0.9, 0.5) for strat in (E.NAIVE, E.GLOBAL, E.NEAREST)]
+        runs += [("chi_cap", 0.9, E.GLOBAL, cap) for cap in (64, 128, 256, 512)]
+        _timed_circuit(E, torch, dev, n_q, qs[:30], ops_dev, 4, f_min=0.9, n_2q=n, chi_max=64, precision=prec)
+        for kind, f_min, strat, cap in runs:
+            stream = torch.cuda.current_stream(dev)
+            m = E.MPS(n_q, f_min=f_min, n_2q=n, strategy=strat, chi_max=cap, precision=prec, log_truncations=True,
+                      stream=stream.cuda_stream)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            E.mps_apply_circuit_device(m.h, qs, ops_dev.data_ptr(), 4)
+            inferred = m.fidelity()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            log = m.truncation_log()
+            emit({"study": "e1", "part": kind, "n_qubits": n_q, "depth": depth, "n_2q": n, "f_min": f_min,
+                  "strategy": names[strat], "chi_cap": cap, "inferred_fidelity": inferred,
+                  "true_fidelity": true_fidelity(m), "gpu_s": e0.elapsed_time(e1) / 1e3,
+                  "max_bond": max(m.bond_dims()), "cap_hits": sum(1 for r in log if r["cap_hit"])})
+            m.close()
     elif a.study == "vidal":
         # (1) inferred against true fidelity, canonical and Vidal form, 18 qubits depth 18
         n_q, depth = 18, 18
