@@ -182,6 +182,18 @@ mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, co
 mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
                                   double target, int concurrency);
 
+/* The per-truncation target f_t of the schedule (Eq. uniform and the strategies
+ * of Fig. 1) before the truncation that follows n_done truncations whose
+ * fidelities multiply to `product`: NAIVE f_t = F_min^(1/n_2q); GLOBAL
+ * f_t = (F_min / product)^(1/m); NEAREST f_t = F_min / (product f0^(m-1)),
+ * m = max(n_2q - n_done, 1); clamped to at most 1, and 1 once product < F_min
+ * or F_min >= 1.  The formula the selection kernel evaluates on the device
+ * (there in CUDA's pow), for callers that drive the stateless update calls.
+ * Host only, no handle.  Errors: MPS_ERR_ARG (strategy out of range, f_min <= 0,
+ * n_2q or n_done < 0, product < 0 or NaN, NULL f_t). */
+mps_status mps_schedule_target(int strategy, double f_min, long long n_2q, long long n_done, double product,
+                               double* f_t);
+
 /* Failure-detection self-test (no trap, no fault: a signal is withheld and a
  * bounded wait runs out).  Every device-side wait of the library gives up at a
  * wall-clock deadline (2 s by default); this call sets the handle's limit to

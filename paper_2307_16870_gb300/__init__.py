@@ -28,7 +28,7 @@ __all__ = [
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
     "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap", "mps_qr_c64",
     "mps_apply_layer_device", "mps_gemm_device", "mps_tsvd_device", "mps_tsvd_backward_device",
-    "mps_selftest_timeout",
+    "mps_selftest_timeout", "mps_schedule_target",
 ]
 
 PURE, MIXED = 0, 1
@@ -138,6 +138,8 @@ def load(path: str | None = None):
         "mps_tsvd_backward_device": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
         "mps_selftest_timeout": (C.c_int, [H, C.c_int, C.c_longlong]),
+        "mps_schedule_target": (C.c_int, [C.c_int, C.c_double, C.c_longlong, C.c_longlong, C.c_double,
+                                          C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +247,14 @@ def mps_tsvd_backward_device(h: int, m: int, n: int, k: int, u: int, s: int, v: 
                                                   C.c_void_p(v), C.c_void_p(aq_bar or None),
                                                   C.c_void_p(ap_bar or None), float(eps), C.c_void_p(a_bar)),
                   "mps_tsvd_backward_device")
+
+
+def mps_schedule_target(strategy: int, f_min: float, n_2q: int, n_done: int, product: float) -> float:
+    """The schedule's per-truncation target (see include/eamps.h)."""
+    out = C.c_double()
+    _check(load().mps_schedule_target(int(strategy), float(f_min), int(n_2q), int(n_done), float(product),
+                                      C.byref(out)), "mps_schedule_target")
+    return out.value
 
 
 def mps_selftest_timeout(h: int, site: int = 0, wait_ns: int = 50_000_000) -> int:
@@ -534,14 +544,6 @@ class MPS:
 
     def stats_reset(self):
         return mps_stats_reset(self.h)
-
-    def contract(self) -> np.ndarray:
-        """All sites contracted on the host (test helper): d^N coefficients."""
-        t = self.site(0).reshape(self.d, -1)
-        for i in range(1, self.n):
-            b = self.site(i)
-            t = (t @ b.reshape(b.shape[0], -1)).reshape(-1, b.shape[2])
-        return t.reshape(-1)
 
 
 load()

@@ -27,7 +27,8 @@ import time
 import numpy as np
 import torch
 
-from . import FP64, MPS, TF32X3, mps_gemm_device, mps_tsvd_backward_device, mps_tsvd_device
+from . import (FP64, GLOBAL, MPS, TF32X3, mps_gemm_device, mps_schedule_target, mps_tsvd_backward_device,
+               mps_tsvd_device)
 
 __all__ = ["Workspace", "gemm", "tsvd", "DiffMPS", "ansatz_gates_torch", "energy_and_grad_ad"]
 
@@ -179,11 +180,11 @@ class DiffMPS:
         return aq, ap, info
 
     def target(self) -> float:
-        """Global schedule before truncation j+1: (F_min / P_j)^(1/(n - j)), 1 once P_j < F_min."""
-        if self.f_min >= 1.0 or self.product < self.f_min:
-            return 1.0
-        rem = max(self.n_2q - self.n_done, 1)
-        return min((self.f_min / self.product) ** (1.0 / rem), 1.0)
+        """Global schedule before truncation j+1, evaluated by the library (mps_schedule_target):
+        (F_min / P_j)^(1/(n - j)), 1 once P_j < F_min.  P_j is the product of the f values the
+        update calls returned, multiplied in gate order in IEEE double precision as the engine's
+        device product is."""
+        return mps_schedule_target(GLOBAL, self.f_min, self.n_2q, self.n_done, self.product)
 
     def move_right(self):
         c = self.centre

@@ -57,6 +57,19 @@ CoopBudget& coop_budget(int device) {
   return budgets[device & 63];
 }
 
+// Per-truncation target of the schedule (Eq. uniform, Fig. 1) before the truncation that follows
+// n_done truncations with running product `product`; the formula of the selection kernel.
+double schedule_target(int strategy, double f_min, long long n_2q, long long n_done, double product) {
+  if (f_min >= 1.0 || product < f_min) return 1.0;
+  const long long rem = std::max<long long>(n_2q - n_done, 1);
+  const double f0 = (f_min < 1.0 && n_2q > 0) ? std::pow(f_min, 1.0 / (double)n_2q) : 1.0;
+  double ft;
+  if (strategy == MPS_NAIVE) ft = f0;
+  else if (strategy == MPS_GLOBAL) ft = std::pow(f_min / product, 1.0 / (double)rem);
+  else ft = f_min / (product * std::pow(f0, (double)(rem - 1)));
+  return std::min(ft, 1.0);
+}
+
 mps_status from_bits(int bits) {
   if (bits & ST_TIMEOUT) return MPS_ERR_TIMEOUT;
   if (bits & ST_NONFINITE) return MPS_ERR_NONFINITE;
@@ -740,18 +753,7 @@ struct Engine final : mps_state {
     mps_status s = read_ctrl();   // everything of this handle done; product and gate count current
     if (s != MPS_OK && s != MPS_WARN_CHI_CAP) return s;
     double ft = target;
-    if (ft < 0.0) {
-      const double p = hctrl->product;
-      if (opt.f_min >= 1.0 || p < opt.f_min) {
-        ft = 1.0;
-      } else {
-        const long long rem = std::max<long long>(opt.n_2q - (long long)hctrl->n_done, 1);
-        if (opt.strategy == MPS_NAIVE) ft = hctrl->f0;
-        else if (opt.strategy == MPS_GLOBAL) ft = std::pow(opt.f_min / p, 1.0 / (double)rem);
-        else ft = opt.f_min / (p * std::pow(hctrl->f0, (double)(rem - 1)));
-        ft = std::min(ft, 1.0);
-      }
-    }
+    if (ft < 0.0) ft = schedule_target(opt.strategy, opt.f_min, opt.n_2q, hctrl->n_done, hctrl->product);
     const int nh = std::min(concurrency, n);
     while ((int)helpers.size() < nh) {
       cudaStream_t hs = nullptr;
@@ -1523,6 +1525,15 @@ mps_status mps_tsvd_backward_device(mps_handle h, int m, int n, int k, const voi
                                     const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) {
   if (!h) return MPS_ERR_ARG;
   return h->tsvd_backward_device(m, n, k, U, S, V, Aq_bar, Ap_bar, eps, A_bar);
+}
+
+mps_status mps_schedule_target(int strategy, double f_min, long long n_2q, long long n_done, double product,
+                               double* f_t) {
+  if (!f_t || strategy < MPS_NAIVE || strategy > MPS_NEAREST || !(f_min > 0.0) || n_2q < 0 || n_done < 0 ||
+      !(product >= 0.0))
+    return MPS_ERR_ARG;
+  *f_t = schedule_target(strategy, f_min, n_2q, n_done, product);
+  return MPS_OK;
 }
 
 mps_status mps_selftest_timeout(mps_handle h, int site, long long wait_ns) {

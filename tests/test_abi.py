@@ -5,6 +5,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import superop as SO
@@ -99,3 +100,22 @@ def test_batch_rejects_bad_arguments_without_touching_the_gpu():
     assert lib.mps_batch_run(None, 2, 1, None) == 1
     assert lib.mps_batch_run(items, 1, 0, None) == 1
     assert lib.mps_batch_run(items, 0, 4, None) == 0
+
+
+def test_schedule_target_matches_the_oracle_schedule():
+    """mps_schedule_target (host code of the library, no GPU) against the oracle's schedule for
+    every strategy, along the products of a made-up sequence of truncation fidelities."""
+    import paper_2307_16870_gb300 as E
+    from oracle import textbook_mps as T
+    rng = np.random.default_rng(3)
+    for strat in (T.NAIVE, T.GLOBAL, T.NEAREST):
+        for f_min in (0.9, 0.5, 0.999):
+            o = T.TextbookMPS(4, f_min=f_min, n_2q=40, strategy=strat)
+            for j in range(45):
+                want = o.scheduled_target()
+                got = E.mps_schedule_target(strat, f_min, 40, o.n_done, o.product)
+                assert abs(got - want) <= 1e-15 * max(1.0, abs(want)), (strat, f_min, j, got, want)
+                o.product *= 1.0 - abs(rng.normal(0.0, 3e-3))
+                o.n_done += 1
+    with pytest.raises(E.MpsError):
+        E.mps_schedule_target(5, 0.9, 10, 0, 1.0)

@@ -17,6 +17,7 @@ E = pytest.importorskip("paper_2307_16870_gb300")
 
 import workloads as W  # noqa: E402
 from oracle import statevector as SV  # noqa: E402
+from tests.helpers import contract_sites  # noqa: E402
 
 SITES = ["flag", "jacobi", "gram", "gemm"]
 
@@ -38,7 +39,7 @@ def test_a_wait_that_runs_out_is_reported_and_the_handle_recovers_after_reset(si
     circ = W.brickwork_circuit(n, 4, 31)
     m.run(circ.gates(), 1.0)
     psi = SV.run_circuit(n, circ.gates())
-    got = m.contract()
+    got = contract_sites(m)
     assert 1.0 - abs(np.vdot(psi, got)) ** 2 / np.vdot(got, got).real < 1e-6
     # another handle on the same context was never affected
     other = E.MPS(n)

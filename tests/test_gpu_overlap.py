@@ -14,6 +14,7 @@ import workloads as W  # noqa: E402
 from oracle import densitymatrix as DM  # noqa: E402
 from oracle import statevector as SV  # noqa: E402
 from oracle import textbook_mps as T  # noqa: E402
+from tests.helpers import contract_sites  # noqa: E402
 
 
 def _run(n, circ, precision=E.TF32X3, f_min=1.0, target=-1.0, **kw):
@@ -28,7 +29,7 @@ def test_overlap_equals_dense_inner_product_and_oracle_true_fidelity():
     exact = _run(n, circ, target=1.0)
     ea = _run(n, circ, f_min=0.95)
     assert max(ea.bond_dims()) < max(exact.bond_dims())       # the EA run did truncate
-    a, b = exact.contract(), ea.contract()
+    a, b = contract_sites(exact), contract_sites(ea)
     ov = exact.overlap(ea)
     assert abs(ov - np.vdot(a, b)) < 1e-12 * max(1.0, abs(ov))
     assert abs(ea.overlap(ea) - np.vdot(b, b)) < 1e-12

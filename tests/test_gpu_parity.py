@@ -24,6 +24,7 @@ from oracle import densitymatrix as DM
 from oracle import statevector as SV
 from oracle import superop as SO
 from oracle import textbook_mps as T
+from tests.helpers import contract_sites  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -83,7 +84,7 @@ def test_untruncated_12q_matches_state_vector(name, prec):
         m.apply_2q(q, u, 1.0)
         svals.append(m.last_singular_values())
     psi = SV.run_circuit(12, circ.gates())
-    got = m.contract()
+    got = contract_sites(m)
     ov = abs(np.vdot(psi, got)) ** 2 / (np.vdot(got, got).real)
     assert ov >= 1.0 - tol["ov"], ov
     orc = T.TextbookMPS(12, n_2q=circ.n_2q, record_svals=True).run(circ.gates(), target=1.0)
@@ -109,7 +110,7 @@ def test_ea_12q_matches_oracle(name, prec, strategy):
         assert abs(m.fidelity() - orc.product) < tol["prod"]
         assert m.bond_dims() == orc.bond_dims()
         psi_o = orc.to_statevector()
-        got = m.contract()
+        got = contract_sites(m)
         assert abs(np.vdot(psi_o, got)) ** 2 / np.vdot(got, got).real >= 1 - 10 * tol["ov"]
     assert m.fidelity() >= 0.99
 
@@ -134,7 +135,7 @@ def test_ragged_shapes_and_all_write_back_modes(name, prec):
         if ncmp == len(orc.log):
             assert m.bond_dims() == orc.bond_dims()
             assert m.centre() == orc.centre
-            got, want = m.contract(), orc.to_statevector()
+            got, want = contract_sites(m), orc.to_statevector()
             assert abs(np.vdot(want, got)) ** 2 >= 1 - 10 * tol["ov"]
 
 
@@ -197,7 +198,7 @@ def test_mpo_untruncated_matches_density_matrix(name, prec):
         rho = DM.apply_kraus(rho, n, q, W.depolarizing_2q_kraus(0.05), 2)
         rho = DM.apply_kraus(rho, n, q, W.amplitude_damping_kraus(0.03), 1)
         rho = DM.apply_kraus(rho, n, q + 1, W.amplitude_damping_kraus(0.03), 1)
-    c = m.contract().reshape((2, 2) * n)
+    c = contract_sites(m).reshape((2, 2) * n)
     perm = list(range(0, 2 * n, 2)) + list(range(1, 2 * n, 2))
     got = c.transpose(perm).reshape(2 ** n, 2 ** n) * math.exp(m.lognorm())
     bound = 64 * (circ.n_2q + 1) * tol["u"] * np.linalg.norm(rho)
@@ -254,7 +255,7 @@ def test_caps_targets_and_single_qubit_ops(name, prec):
             v = W.haar_unitary(2, 6, j)
             m2.apply_1q((q + 3) % n, v)
             o2.apply_1q((q + 3) % n, v)
-    got = m2.contract()
+    got = contract_sites(m2)
     assert abs(np.vdot(o2.to_statevector(), got)) ** 2 >= 1 - 10 * tol["ov"]
 
 
@@ -270,8 +271,8 @@ def test_mixed_single_qubit_channel():
         m.apply_1q((q + 2) % n, ad)
         o.apply_1q((q + 2) % n, ad)
     assert abs(m.lognorm() - o.lognorm) < 1e-10
-    assert np.abs(m.contract() - o.contract()).max() < 1e-10 or \
-        abs(abs(np.vdot(m.contract(), o.contract())) - 1) < 1e-10
+    assert np.abs(contract_sites(m) - o.contract()).max() < 1e-10 or \
+        abs(abs(np.vdot(contract_sites(m), o.contract())) - 1) < 1e-10
 
 
 def test_argument_errors_and_sweep_limit():

@@ -2,6 +2,7 @@
 R upper triangular, and against LAPACK's R (same real-diagonal convention)."""
 import numpy as np
 import pytest
+from tests.helpers import contract_sites  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -90,7 +91,7 @@ def test_circuit_with_qr_modes_matches_oracle(mode):
     assert m.bond_dims() == o.bond_dims()
     assert abs(m.fidelity() - o.product) < 1e-4
     psi = SV.run_circuit(n, circ.gates())
-    got = m.contract()
+    got = contract_sites(m)
     f_true = abs(np.vdot(psi, got)) ** 2 / np.vdot(got, got).real
     f_orc = abs(np.vdot(psi, o.to_statevector())) ** 2
     assert abs(f_true - f_orc) < 1e-4

@@ -19,6 +19,7 @@ import workloads as W  # noqa: E402
 from oracle import statevector as SV  # noqa: E402
 from oracle import textbook_mps as T  # noqa: E402
 from oracle.diff_chain import tsvd as o_tsvd  # noqa: E402
+from tests.helpers import contract_sites  # noqa: E402
 
 if E is not None:
     from paper_2307_16870_gb300 import autodiff as AD  # noqa: E402
@@ -56,7 +57,7 @@ def test_untruncated_circuit_through_the_gram_layout():
     circ = W.brickwork_circuit(n, depth, 1203)
     m = E.MPS(n, n_2q=circ.n_2q, precision=E.TF32X3, svd_kernel=E.SVD_GRAM).run(circ.gates(), 1.0)
     psi = SV.run_circuit(n, circ.gates())
-    got = m.contract()
+    got = contract_sites(m)
     ov = abs(np.vdot(psi, got)) ** 2 / np.vdot(got, got).real
     assert ov > 1 - 1e-6, ov
     assert max(m.bond_dims()) == 2 ** (n // 2)

@@ -10,6 +10,7 @@ E = pytest.importorskip("paper_2307_16870_gb300")
 import workloads as W  # noqa: E402
 from oracle import statevector as SV  # noqa: E402
 from oracle.vidal import VidalMPS  # noqa: E402
+from tests.helpers import contract_sites  # noqa: E402
 
 
 def _norm(v):
@@ -23,7 +24,7 @@ def test_untruncated_vidal_matches_the_state_vector(prec):
     m = E.MPS(n, n_2q=circ.n_2q, precision=prec, vidal=True).run(circ.gates(), 1.0)
     psi = SV.run_circuit(n, circ.gates())
     tol = 1e-12 if prec == E.FP64 else 1e-6
-    assert 1.0 - abs(np.vdot(psi, _norm(m.contract()))) ** 2 < tol
+    assert 1.0 - abs(np.vdot(psi, _norm(contract_sites(m)))) ** 2 < tol
     assert m.centre() == 0
     m.close()
 
@@ -39,7 +40,7 @@ def test_ea_vidal_matches_the_vidal_oracle(prec, seed, f_min):
         o.apply_2q(q, u)
     assert m.bond_dims() == o.bond_dims()
     assert abs(m.fidelity() - o.product) < (1e-10 if prec == E.FP64 else 1e-4)
-    ov = abs(np.vdot(_norm(o.to_statevector()), _norm(m.contract()))) ** 2
+    ov = abs(np.vdot(_norm(o.to_statevector()), _norm(contract_sites(m)))) ** 2
     assert 1.0 - ov < (1e-12 if prec == E.FP64 else 1e-5)
     # the amplitude chain works on the Vidal form (no centre move)
     bits = [0] * n
@@ -103,7 +104,7 @@ def test_layer_runs_match_the_oracle_layer_by_layer(prec):
     for r, ro in zip(log, o.log):
         assert r["q"] == ro["q"] and r["k"] == ro["k"]
         assert abs(r["f_t"] - ro["f_t"]) < (1e-12 if prec == E.FP64 else 1e-5)
-    ov = abs(np.vdot(_norm(o.to_statevector()), _norm(m.contract()))) ** 2
+    ov = abs(np.vdot(_norm(o.to_statevector()), _norm(contract_sites(m)))) ** 2
     assert 1.0 - ov < (1e-12 if prec == E.FP64 else 1e-5)
     assert m.stats()["gates"] == circ.n_2q
     m.close()
