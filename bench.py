@@ -362,6 +362,7 @@ def run_ours(a) -> int:
         extras["time_to_target"] = time_to_target(E, torch, dev, a, prec)
         extras["chi512"] = chi512_throughput(E, torch, dev, a, prec, circ, ops_dev, qs)
         extras["precision_vs_fp64"] = precision_vs_fp64(E, a, prec, circ)
+    extras["svd_layout_tuning"] = svd_tuning_summary(E)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_oracle_sample(circ, a, a.cpu_sample_s)
@@ -428,10 +429,25 @@ def time_to_target(E, torch, dev, a, prec) -> dict:
             "ea_time_over_fixed": ea_s / fx_s}
 
 
+def svd_tuning_summary(E) -> dict:
+    """The Jacobi layout autotuner's choices so far in this process (shape classes of the SVD,
+    rows and columns rounded up to 64): how many classes were timed and where each layout won."""
+    tab = E.mps_svd_tuning()
+    gram = [f"{t['rows']}x{t['cols']}{'+W' if t['accumulate'] else ''}" for t in tab if t["layout"] == "gram"]
+    ratios = [t["ms_gram"] / t["ms_tournament"] for t in tab if t["ms_gram"] > 0 and t["ms_tournament"] > 0]
+    return {"classes": len(tab), "gram_classes": gram,
+            "gram_over_tournament_time": {"min": min(ratios), "max": max(ratios)} if ratios else None}
+
+
 def chi512_throughput(E, torch, dev, a, prec, circ, ops_dev, qs) -> dict:
     """Fixed bond 512 (the largest fixed-chi point of the pure-state benchmark) on the same circuit:
     every saturated update is a 1024 x 1024 SVD."""
     n = circ.n_2q
+    # the saturated 1024 x 1024 SVD's layout is tuned before the clock starts (once per process)
+    t = E.MPS(a.n_qubits, fixed_chi=512, chi_max=512, precision=prec, svd_kernel=svd_kernel_of(a, E))
+    for acc in (False, True):
+        t.svd_tune(1024, 1024, acc)
+    t.close()
     ms, fid, mx, jms, jl = _timed_circuit(E, torch, dev, a.n_qubits, qs, ops_dev, 4, n_2q=n, fixed_chi=512,
                                           chi_max=512, precision=prec, svd_kernel=svd_kernel_of(a, E))
     return {"workload": f"same circuit, fixed chi = 512 ({n} gates)", "updates_per_s": n / (ms / 1e3),

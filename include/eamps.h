@@ -182,6 +182,29 @@ mps_status mps_apply_circuit_device(mps_handle h, int n_gates, const int* qs, co
 mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, const double* ops_dev, int op_dim,
                                   double target, int concurrency);
 
+/* The Jacobi layout autotuner's table for the current device (this process).
+ * Under MPS_SVD_AUTO, the first time a handle that runs alone meets a shape
+ * class of the SVD's matrix (rows and columns rounded up to multiples of 64,
+ * whether rotations are accumulated) with at least 256 columns, both layouts of
+ * the one-sided Jacobi are timed on a synthetic matrix of the shape it met; the
+ * Gram block layout is kept for the class when it is at least 10 % faster.
+ * Fills up to `cap` entries (class rows and columns, accumulated rotations 0/1,
+ * chosen layout MPS_SVD_TOURNAMENT / MPS_SVD_GRAM, or MPS_SVD_AUTO when neither
+ * could be timed and the fixed size rule applies, and the two times in ms, -1
+ * where a layout does not apply) and returns the number of entries (-1 on a
+ * CUDA error).  With cap 0 and null pointers it only counts.  Host only. */
+int mps_svd_tuning(int cap, int* rows, int* cols, int* accumulate, int* layout, double* ms_tournament,
+                   double* ms_gram);
+
+/* Tune the Jacobi layout of one shape class ahead of use (the timing runs the
+ * autotuner would otherwise make inside the first SVD of that class, see
+ * mps_svd_tuning); also runs for a handle built for concurrent use, on its own
+ * stream.  rows, cols: 1..the handle's largest matrix side; accumulate: 0/1.
+ * *layout (may be null) receives the layout the class now uses (the handle's
+ * own svd_kernel when that is not MPS_SVD_AUTO, or below 256 columns).  Blocks
+ * until the timing runs end.  MPS_ERR_ARG on bad sizes. */
+mps_status mps_svd_tune(mps_handle h, int rows, int cols, int accumulate, int* layout);
+
 /* The per-truncation target f_t of the schedule (Eq. uniform and the strategies
  * of Fig. 1) before the truncation that follows n_done truncations whose
  * fidelities multiply to `product`: NAIVE f_t = F_min^(1/n_2q); GLOBAL

@@ -28,7 +28,7 @@ __all__ = [
     "mps_reset", "mps_profile", "mps_stats", "mps_stats_reset", "MpsStats", "mps_cgemm_c64",
     "mps_set_site", "mps_set_centre", "mps_cgemm_c64_noalloc", "BatchItem", "mps_batch_run", "mps_overlap", "mps_qr_c64",
     "mps_apply_layer_device", "mps_gemm_device", "mps_tsvd_device", "mps_tsvd_backward_device",
-    "mps_selftest_timeout", "mps_schedule_target",
+    "mps_selftest_timeout", "mps_schedule_target", "mps_svd_tuning", "mps_svd_tune",
 ]
 
 PURE, MIXED = 0, 1
@@ -138,6 +138,9 @@ def load(path: str | None = None):
         "mps_tsvd_backward_device": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
         "mps_selftest_timeout": (C.c_int, [H, C.c_int, C.c_longlong]),
+        "mps_svd_tune": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+        "mps_svd_tuning": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "mps_schedule_target": (C.c_int, [C.c_int, C.c_double, C.c_longlong, C.c_longlong, C.c_double,
                                           C.POINTER(C.c_double)]),
     }
@@ -249,11 +252,33 @@ def mps_tsvd_backward_device(h: int, m: int, n: int, k: int, u: int, s: int, v: 
                   "mps_tsvd_backward_device")
 
 
+def mps_svd_tuning() -> list[dict]:
+    """The Jacobi layout autotuner's table for the current device (see include/eamps.h)."""
+    lib = load()
+    n = lib.mps_svd_tuning(0, None, None, None, None, None, None)
+    if n <= 0:
+        return []
+    ib = [(C.c_int * n)() for _ in range(4)]
+    db = [(C.c_double * n)() for _ in range(2)]
+    lib.mps_svd_tuning(n, *ib, *db)
+    names = {SVD_TOURNAMENT: "tournament", SVD_GRAM: "gram", SVD_AUTO: "rule"}
+    return [{"rows": ib[0][i], "cols": ib[1][i], "accumulate": bool(ib[2][i]), "layout": names.get(ib[3][i], "?"),
+             "ms_tournament": db[0][i], "ms_gram": db[1][i]} for i in range(n)]
+
+
 def mps_schedule_target(strategy: int, f_min: float, n_2q: int, n_done: int, product: float) -> float:
     """The schedule's per-truncation target (see include/eamps.h)."""
     out = C.c_double()
     _check(load().mps_schedule_target(int(strategy), float(f_min), int(n_2q), int(n_done), float(product),
                                       C.byref(out)), "mps_schedule_target")
+    return out.value
+
+
+def mps_svd_tune(h: int, rows: int, cols: int, accumulate: bool = False) -> int:
+    """Tune the Jacobi layout of one shape class ahead of use; returns the layout it now uses."""
+    out = C.c_int(0)
+    _check(load().mps_svd_tune(C.c_void_p(h), int(rows), int(cols), int(bool(accumulate)), C.byref(out)),
+           "mps_svd_tune")
     return out.value
 
 
@@ -464,6 +489,9 @@ class MPS:
         obj = cls.__new__(cls)
         obj.n, obj.kind, obj.d, obj.h = n_qubits, kind, 2 if kind == PURE else 4, handle
         return obj
+
+    def svd_tune(self, rows: int, cols: int, accumulate: bool = False) -> int:
+        return mps_svd_tune(self.h, rows, cols, accumulate)
 
     def close(self):
         if getattr(self, "h", None):

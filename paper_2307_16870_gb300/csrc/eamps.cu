@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstddef>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -68,6 +69,48 @@ double schedule_target(int strategy, double f_min, long long n_2q, long long n_d
   else if (strategy == MPS_GLOBAL) ft = std::pow(f_min / product, 1.0 / (double)rem);
   else ft = f_min / (product * std::pow(f0, (double)(rem - 1)));
   return std::min(ft, 1.0);
+}
+
+// ---------------------------------------------------------------- Jacobi layout autotuner
+// The first time a handle meets a shape class (rows and columns rounded up to kTuneGrain,
+// accumulation) with at least kTuneMinCols columns under MPS_SVD_AUTO, it times both layouts of
+// the one-sided Jacobi (the tournament kernels and the Gram-matrix block kernel) on a synthetic
+// matrix of the shape it met and keeps the faster one for the process (the block kernel only when
+// at least 10 % faster, so that near ties do not flip between runs).  Every real SVD of that class
+// then runs the chosen layout.  The classes keep the number of timing runs small on circuits whose
+// bonds take many values.
+constexpr int kTuneMinCols = 256;
+constexpr int kTuneGrain = 64;
+struct TuneKey {
+  int dev, l, c, acc;   // l, c: upper bounds of the class
+  bool operator<(const TuneKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (l != o.l) return l < o.l;
+    if (c != o.c) return c < o.c;
+    return acc < o.acc;
+  }
+};
+struct TuneEntry {
+  int kind;
+  double ms_tournament, ms_gram;
+};
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::map<TuneKey, TuneEntry>& tune_table() {
+  static std::map<TuneKey, TuneEntry> t;
+  return t;
+}
+
+// Deterministic synthetic matrix for the timing runs: entries uniform in [-1, 1) from a hash of
+// the index (the values only set the Jacobi's sweep count, as a random matrix does).
+__global__ void synthetic_fill_kernel(float2* __restrict__ x, long long n, unsigned seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull + seed;
+    h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29; h *= 0x94D049BB133111EBull; h ^= h >> 32;
+    x[i] = make_float2((float)(h & 0xFFFFFF) / 8388608.f - 1.f, (float)((h >> 24) & 0xFFFFFF) / 8388608.f - 1.f);
+  }
 }
 
 mps_status from_bits(int bits) {
@@ -136,6 +179,7 @@ struct mps_state {
   virtual mps_status tsvd_backward_device(int m, int n, int k, const void* U, const double* S, const void* V,
                                           const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) = 0;
   virtual mps_status selftest_timeout(int site, long long wait_ns) = 0;
+  virtual mps_status svd_tune(int l, int c, int acc, int* layout) = 0;
   int N = 0;
   int d = 2;
   int centre = 0;
@@ -422,13 +466,11 @@ struct Engine final : mps_state {
     return cu(cudaMemcpyAsync(dst, src, sizeof(Z) * count, cudaMemcpyDeviceToDevice, stream));
   }
 
-  mps_status run_jacobi(int l, int c, bool acc, Z* Xp, long long ldx) {
-    last_c = c;
-    if (acc)
-      if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
-    if (c <= 1) return MPS_OK;
-    JacobiPlan plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count, opt.svd_kernel);
-    if (plan.gram_R == 0) {   // (the Gram layout is checked for residency when it is planned)
+  // Launch plan of one Jacobi SVD for a layout kind, with the co-residency check of the
+  // tournament kernels (the Gram layout is checked when it is planned).
+  mps_status make_plan(int l, int c, bool acc, int kind, JacobiPlan& plan) {
+    plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count, kind);
+    if (plan.gram_R == 0) {
       const int fit = plan.cluster > 0 ? plan.cluster : jacobi_max_ctas<R>(plan);
       if (fit <= 0) return MPS_ERR_CUDA;
       if (plan.nb / 2 > fit) {
@@ -436,6 +478,79 @@ struct Engine final : mps_state {
         if (plan.nb / 2 > fit) return MPS_ERR_ARG;
       }
     }
+    return MPS_OK;
+  }
+
+  // The layout kind for a shape: the option, or under MPS_SVD_AUTO the tuned choice (measured on
+  // first use of the shape when this handle runs alone on the GPU; the fixed rule otherwise).
+  int layout_for(int l, int c, bool acc, bool force = false) {
+    if (!std::is_same<R, float>::value || opt.svd_kernel != MPS_SVD_AUTO || c < kTuneMinCols) return opt.svd_kernel;
+    const auto up = [](int v) { return (v + kTuneGrain - 1) / kTuneGrain * kTuneGrain; };
+    const TuneKey key{device, up(l), up(c), acc ? 1 : 0};
+    {
+      std::lock_guard<std::mutex> lk(tune_mutex());
+      auto it = tune_table().find(key);
+      if (it != tune_table().end()) return it->second.kind;
+    }
+    if (shared_gpu && !force) return MPS_SVD_AUTO;   // no timing runs beside other handles' kernels
+    double ms[2] = {-1.0, -1.0};
+    const int kinds[2] = {MPS_SVD_TOURNAMENT, MPS_SVD_GRAM};
+    const long long nx = (long long)l * c, nw = acc ? (long long)c * c : 0;
+    Z* xt = nullptr;
+    DevCtrl* tc = nullptr;
+    cudaEvent_t e0 = ev_get(), e1 = ev_get();
+    if (cudaMalloc(&xt, sizeof(Z) * (nx + nw + 1)) == cudaSuccess && cudaMalloc(&tc, sizeof(DevCtrl)) == cudaSuccess) {
+      for (int v = 0; v < 2; ++v) {
+        JacobiPlan plan;
+        if (make_plan(l, c, acc, kinds[v], plan) != MPS_OK) continue;
+        if (kinds[v] == MPS_SVD_GRAM && plan.gram_R == 0) continue;
+        double best = -1.0;
+        for (int rep = 0; rep < 2; ++rep) {
+          synthetic_fill_kernel<<<256, 256, 0, stream>>>(reinterpret_cast<float2*>(xt), nx, 12345u);
+          if (acc) set_identity<R>(xt + nx, c, c, stream);
+          cudaMemsetAsync(tc, 0, sizeof(DevCtrl), stream);
+          cudaEventRecord(e0, stream);
+          cudaError_t e = jacobi_launch<R>(plan, xt, l, l, c, acc ? xt + nx : nullptr, c, opt.max_sweeps, tc, xch,
+                                           xch_cap, jflags, kFlagsCap, stream);
+          cudaEventRecord(e1, stream);
+          int st = 1;
+          if (e == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess)
+            cudaMemcpy(&st, &tc->status, sizeof(int), cudaMemcpyDeviceToHost);
+          float t = 0.f;
+          if (st == 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) best = (best < 0.0) ? t : std::min(best, (double)t);
+          cudaGetLastError();
+        }
+        ms[v] = best;
+      }
+    }
+    cudaGetLastError();
+    if (xt) cudaFree(xt);
+    if (tc) cudaFree(tc);
+    ev_pool.push_back(e0);
+    ev_pool.push_back(e1);
+    int kind = MPS_SVD_TOURNAMENT;
+    if (ms[1] > 0.0 && (ms[0] < 0.0 || ms[1] < 0.9 * ms[0])) kind = MPS_SVD_GRAM;
+    if (ms[0] < 0.0 && ms[1] < 0.0) kind = MPS_SVD_AUTO;   // no measurement: the fixed rule
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    auto ins = tune_table().emplace(key, TuneEntry{kind, ms[0], ms[1]});
+    return ins.first->second.kind;
+  }
+
+  mps_status svd_tune(int l, int c, int acc, int* layout) override {
+    if (l < 1 || c < 1 || l > c_max || c > c_max) return MPS_ERR_ARG;
+    if (mps_status s = sync()) return s;
+    const int kind = layout_for(l, c, acc != 0, true);
+    if (layout) *layout = kind;
+    return cu(cudaStreamSynchronize(stream));
+  }
+
+  mps_status run_jacobi(int l, int c, bool acc, Z* Xp, long long ldx) {
+    last_c = c;
+    if (acc)
+      if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
+    if (c <= 1) return MPS_OK;
+    JacobiPlan plan;
+    if (mps_status s = make_plan(l, c, acc, layout_for(l, c, acc), plan)) return s;
     if (mps_status s = coop_ensure(jacobi_plan_ctas(plan))) return s;
     ++n_jac;
     if (in_move) ++n_jac_move;
@@ -1527,6 +1642,27 @@ mps_status mps_tsvd_backward_device(mps_handle h, int m, int n, int k, const voi
   return h->tsvd_backward_device(m, n, k, U, S, V, Aq_bar, Ap_bar, eps, A_bar);
 }
 
+int mps_svd_tuning(int cap, int* rows, int* cols, int* accumulate, int* layout, double* ms_tournament,
+                   double* ms_gram) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lk(tune_mutex());
+  int n = 0;
+  for (const auto& kv : tune_table()) {
+    if (kv.first.dev != dev) continue;
+    if (n < cap && rows && cols && accumulate && layout && ms_tournament && ms_gram) {
+      rows[n] = kv.first.l;
+      cols[n] = kv.first.c;
+      accumulate[n] = kv.first.acc;
+      layout[n] = kv.second.kind;
+      ms_tournament[n] = kv.second.ms_tournament;
+      ms_gram[n] = kv.second.ms_gram;
+    }
+    ++n;
+  }
+  return n;
+}
+
 mps_status mps_schedule_target(int strategy, double f_min, long long n_2q, long long n_done, double product,
                                double* f_t) {
   if (!f_t || strategy < MPS_NAIVE || strategy > MPS_NEAREST || !(f_min > 0.0) || n_2q < 0 || n_done < 0 ||
@@ -1539,6 +1675,11 @@ mps_status mps_schedule_target(int strategy, double f_min, long long n_2q, long 
 mps_status mps_selftest_timeout(mps_handle h, int site, long long wait_ns) {
   if (!h) return MPS_ERR_ARG;
   return h->selftest_timeout(site, wait_ns);
+}
+
+mps_status mps_svd_tune(mps_handle h, int rows, int cols, int accumulate, int* layout) {
+  if (!h) return MPS_ERR_ARG;
+  return h->svd_tune(rows, cols, accumulate, layout);
 }
 
 mps_status mps_fidelity(mps_handle h, double* inferred) {

@@ -1,9 +1,9 @@
 """The two layouts of the one-sided Jacobi SVD against the FP64 oracle (LAPACK's SVD).
 
 mps_options.svd_kernel selects the tournament kernels (MPS_SVD_TOURNAMENT) or the block kernel
-with Gram-matrix inner sweeps over thread-block clusters (MPS_SVD_GRAM); the automatic choice uses
-the latter only from 1024 columns on, so these tests force it at sizes the oracle finishes in
-seconds: several slots and rounds, ragged column counts (zero padding columns), both orientations,
+with Gram-matrix inner sweeps over thread-block clusters (MPS_SVD_GRAM).  The automatic choice
+times both on the first use of a shape class from 256 columns on and keeps the faster; these
+tests force each layout at sizes the oracle finishes in seconds: several slots and rounds, ragged column counts (zero padding columns), both orientations,
 and accumulated rotations (the rows of W below those of X).  Tolerances as everywhere for the
 complex64 path: retained singular values 1e-5 relative on identical inputs, untruncated overlap
 1 - 1e-6, vectors orthonormal to 1e-5."""
@@ -86,3 +86,58 @@ def test_accumulated_rotations_match_the_oracle(m, n, ws_gram):
     rel = np.abs(s_gpu - r["S"][:k]) / r["S"][:k]
     assert rel.max() < 1e-5, rel.max()
     assert np.abs(aq @ ap - r["Aq"] @ r["Ap"]).max() < 1e-5 * np.abs(r["Aq"] @ r["Ap"]).max() * 10
+
+
+def test_autotuner_times_both_layouts_and_keeps_the_faster():
+    """mps_svd_tune on a 512 x 512 class (with and without accumulated rotations): the table then
+    holds both timings, and the kept layout is the block kernel exactly when it was at least 10 %
+    faster.  A second call does not time again."""
+    m = E.MPS(100, chi_max=256, precision=E.TF32X3)
+    for acc in (False, True):
+        layout = m.svd_tune(512, 512, acc)
+        assert layout in (E.SVD_TOURNAMENT, E.SVD_GRAM)
+    tab = {(t["rows"], t["cols"], t["accumulate"]): t for t in E.mps_svd_tuning()}
+    for acc in (False, True):
+        t = tab[(512, 512, acc)]
+        assert t["ms_tournament"] > 0 and t["ms_gram"] > 0
+        assert (t["layout"] == "gram") == (t["ms_gram"] < 0.9 * t["ms_tournament"])
+    # the class of 500 x 470 is that of 512 x 512: no new timing run
+    before = len(E.mps_svd_tuning())
+    m.svd_tune(500, 470, False)
+    assert len(E.mps_svd_tuning()) == before
+    m.close()
+
+
+def test_autotuner_respects_a_forced_layout_and_small_shapes():
+    m = E.MPS(100, chi_max=256, precision=E.TF32X3, svd_kernel=E.SVD_TOURNAMENT)
+    assert m.svd_tune(512, 512) == E.SVD_TOURNAMENT
+    m.close()
+    m = E.MPS(100, chi_max=256, precision=E.TF32X3)
+    assert m.svd_tune(128, 128) == E.SVD_AUTO      # below 256 columns: the fixed rule, no timing
+    with pytest.raises(Exception):
+        m.svd_tune(0, 512)
+    with pytest.raises(Exception):
+        m.svd_tune(512, 4096)
+    m.close()
+
+
+def test_tuned_automatic_choice_keeps_parity_at_theta_512():
+    """After tuning, the automatic choice runs whichever layout won; the update still matches the
+    oracle (retained singular values 1e-5 relative, same k)."""
+    n, cap, centre, q = 100, 256, 50, 50
+    sites, _ = W.random_canonical_mps(n, cap, centre, seed=950)
+    u = W.haar_unitary(4, 951, q)
+    orc = T.TextbookMPS(n, record_svals=True, chi_max=cap)
+    orc.sites = [s.copy() for s in sites]
+    orc.centre = centre
+    rec = orc.apply_2q(q, u, target=0.99)
+    m = E.MPS(n, chi_max=cap, precision=E.TF32X3)
+    m.svd_tune(512, 512, False)
+    m.svd_tune(512, 512, True)
+    m.load_sites(sites, centre)
+    m.apply_2q(q, u, 0.99)
+    k = rec["k"]
+    assert m.truncation_log()[-1]["k"] == k
+    rel = np.abs(m.last_singular_values()[:k] - rec["s"][:k]) / rec["s"][:k]
+    assert rel.max() < 1e-5, rel.max()
+    m.close()
