@@ -68,8 +68,8 @@ struct JacobiPlan {
                              // cluster of gram_R CTAs per slot of two 16-column blocks, nb / 2 slots
   int gram_mr = 0;           // rows of the stacked [X; W] held by each CTA of that kernel
 };
-// kind: kJacobiAuto (the Gram-matrix block kernel from kGramMinCols columns on, else the
-// tournament kernels), kJacobiTournament (the cluster / point-to-point kernels only), kJacobiGram
+// kind: kJacobiAuto (the fixed rule, used where the engine has no measured choice for the shape:
+// the Gram-matrix block kernel from kGramMinCols columns on, else the tournament kernels), kJacobiTournament (the cluster / point-to-point kernels only), kJacobiGram
 // (the Gram-matrix block kernel whenever a layout fits, from 64 columns on).  Measured on GB300
 // (complex64, square theta): the two layouts take the same time at 512 columns (7.7 ms, 13 sweeps)
 // and the Gram kernel wins at 1024 (21.2 ms against 24.9 ms); below 512 the tournament kernels win.
