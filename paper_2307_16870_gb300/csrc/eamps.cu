@@ -544,13 +544,17 @@ struct Engine final : mps_state {
     return cu(cudaStreamSynchronize(stream));
   }
 
-  mps_status run_jacobi(int l, int c, bool acc, Z* Xp, long long ldx) {
+  // early_stop: the sweep after which the rotations are below sqrt(tol) is the last (a gate SVD,
+  // whose singular values are recomputed from theta); false where the rotated columns themselves
+  // must be orthonormal to the full tolerance (the Jacobi orthogonalisation of a centre move).
+  mps_status run_jacobi(int l, int c, bool acc, Z* Xp, long long ldx, bool early_stop = true) {
     last_c = c;
     if (acc)
       if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
     if (c <= 1) return MPS_OK;
     JacobiPlan plan;
     if (mps_status s = make_plan(l, c, acc, layout_for(l, c, acc), plan)) return s;
+    plan.early_stop = early_stop;
     if (mps_status s = coop_ensure(jacobi_plan_ctas(plan))) return s;
     ++n_jac;
     if (in_move) ++n_jac_move;
@@ -568,8 +572,7 @@ struct Engine final : mps_state {
   // (l x min(l, c), column-major, ld ldq).
   mps_status qr_run(int l, int c, Z* Xp, long long ldx, Z* Q, long long ldq) {
     if constexpr (std::is_same<R, float>::value) {
-      const int ctas = qr_ctas(l, c, qr_fit);
-      if (mps_status s = coop_ensure(ctas)) return s;
+      const int ctas = qr_ctas(l, c, qr_fit);   // one cluster: no co-residency budget needed
       ++n_qr;
       const int id = tbegin();
       mps_status s = kl(qr_factor(Xp, ldx, l, c, qr_tau, qr_T, ctrl, ctas, stream));
@@ -623,7 +626,7 @@ struct Engine final : mps_state {
     } else if (n <= m) {
       // X = C column-major; C W = Y; Q = Y/|Y| (m x n), R = Q^dagger C, A_{c+1} <- R A_{c+1}
       if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;
-      if ((s = run_jacobi(m, n, false, X, m))) return s;
+      if ((s = run_jacobi(m, n, false, X, m, false))) return s;
       if ((s = kl(column_norms<R>(X, m, m, n, norms, stream)))) return s;
       if ((s = extract(tmp, 1, n, n, m, X, m, 1, nullptr, 0, norms, 0))) return s;       // Q, row-major m x n
       if ((s = gemm(n, n, m, R(1), tmp, 1, n, 1, C, n, 1, 0, tmp2, n, 1))) return s;       // R = Q^dagger C
@@ -634,7 +637,7 @@ struct Engine final : mps_state {
       // X = C^dagger (column i = conj of row i of C), accumulate W (m x m):
       // C^dagger W = Y  ->  C = W Y^dagger: Q = W with unit columns, R = Q^dagger C
       if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;
-      if ((s = run_jacobi(n, m, true, X, n))) return s;
+      if ((s = run_jacobi(n, m, true, X, n, false))) return s;
       if ((s = kl(column_norms<R>(Wacc, m, m, m, norms, stream)))) return s;
       if ((s = extract(tmp, 1, m, m, m, Wacc, m, 1, nullptr, 0, norms, 0))) return s;      // Q row-major m x m
       if ((s = gemm(m, n, m, R(1), tmp, 1, m, 1, C, n, 1, 0, tmp2, n, 1))) return s;       // R = Q^dagger C
@@ -667,7 +670,7 @@ struct Engine final : mps_state {
     } else if (m <= n) {
       // X = C^dagger; C^dagger W = Y -> C = (W S) Yn^dagger: Q' = Yn^dagger (m x n), L = C Q'^dagger
       if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;
-      if ((s = run_jacobi(n, m, false, X, n))) return s;
+      if ((s = run_jacobi(n, m, false, X, n, false))) return s;
       if ((s = kl(column_norms<R>(X, n, n, m, norms, stream)))) return s;
       if ((s = extract(tmp, n, 1, m, n, X, n, 1, nullptr, 1, norms, 0))) return s;        // Q' row-major m x n
       if ((s = gemm(m, m, n, R(1), C, n, 1, 0, tmp, 1, n, 1, tmp2, m, 1))) return s;       // L = C Q'^dagger
@@ -678,7 +681,7 @@ struct Engine final : mps_state {
       // X = C column-major, accumulate W (n x n): C W = Y -> C = Y W^dagger:
       // Q' = W^dagger with unit rows, L = C Q'^dagger
       if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;
-      if ((s = run_jacobi(m, n, true, X, m))) return s;
+      if ((s = run_jacobi(m, n, true, X, m, false))) return s;
       if ((s = kl(column_norms<R>(Wacc, n, n, n, norms, stream)))) return s;
       if ((s = extract(tmp, n, 1, n, n, Wacc, n, 1, nullptr, 1, norms, 0))) return s;      // Q' row-major n x n
       if ((s = gemm(m, n, n, R(1), C, n, 1, 0, tmp, 1, n, 1, tmp2, n, 1))) return s;       // L = C Q'^dagger

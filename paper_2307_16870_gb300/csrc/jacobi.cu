@@ -1075,7 +1075,7 @@ cudaError_t jacobi_launch(const JacobiPlan& plan, cplx<R>* X, long long ldx, int
   a.tol = R(4) * std::sqrt(R(std::max(l, 1))) * Eps<R>::v;
   // quadratic convergence: after a sweep whose pair cosines were all at most sqrt(tol), the next
   // sweep's are at the rounding level, so that sweep is not run
-  a.tol_stop = std::sqrt(a.tol);
+  a.tol_stop = plan.early_stop ? std::sqrt(a.tol) : a.tol;
   a.ctrl = ctrl;
   a.xch = xch;
   a.flags = flags;

@@ -612,7 +612,7 @@ cudaError_t jacobi_gram_launch(const JacobiPlan& plan, float2* X, long long ldx,
   a.nb = plan.nb; a.S = S; a.R = R; a.mr = plan.gram_mr;
   a.max_sweeps = max_sweeps;
   a.tol = 4.f * std::sqrt((float)std::max(l, 1)) * FLT_EPSILON;
-  a.tol_stop = std::sqrt(a.tol);   // as the tournament kernels: the quadratic phase ends one sweep early
+  a.tol_stop = plan.early_stop ? std::sqrt(a.tol) : a.tol;   // as the tournament kernels
   a.ctrl = ctrl;
   a.xbuf = xch;
   a.flags = flags;

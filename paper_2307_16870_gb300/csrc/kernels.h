@@ -46,7 +46,8 @@ cudaError_t store_lambda(double* lam_out, const double* s_sorted, const DevCtrl*
 // Householder QR of the l x c complex64 matrix X (column-major, leading dimension ldx), in place:
 // R in the upper trapezoid, the reflector vectors (unit leading entry implicit) below the
 // diagonal, tau (min(l, c) entries) and the block-reflector factors Tm (32 x 32 per panel of
-// 32 columns).  Rows l <= qr_max_rows().  ctas > 1: cooperative launch (at most qr_max_ctas()).
+// 32 columns).  Rows l <= qr_max_rows().  One launch is one thread-block cluster of ctas CTAs
+// (qr_ctas(); at most qr_max_ctas()), so it waits on no other work of the device.
 int qr_max_rows();
 int qr_max_ctas();
 int qr_ctas(int l, int c, int max_ctas);
@@ -67,6 +68,8 @@ struct JacobiPlan {
   int gram_R = 0;            // > 0: block Jacobi with Gram-matrix inner sweeps (jacobi_gram.cu), one
                              // cluster of gram_R CTAs per slot of two 16-column blocks, nb / 2 slots
   int gram_mr = 0;           // rows of the stacked [X; W] held by each CTA of that kernel
+  bool early_stop = true;    // end after the first sweep whose pair cosines are all <= sqrt(tol);
+                             // false: only after a sweep with no rotation above tol
 };
 // kind: kJacobiAuto (the fixed rule, used where the engine has no measured choice for the shape:
 // the Gram-matrix block kernel from kGramMinCols columns on, else the tournament kernels), kJacobiTournament (the cluster / point-to-point kernels only), kJacobiGram

@@ -5,17 +5,19 @@
 // converges in fewer sweeps, and its rotated, normalised columns are the right
 // singular vectors of X.
 //
-// Design (sm_103a): one persistent cooperative kernel.  Per panel of 32 columns,
-// CTA 0 factors the panel in shared memory (one thread per row, 512 threads,
-// rows <= 512) and forms the triangular factor T of the block reflector
-// Q_panel = I - V T V^dagger; after a grid barrier every CTA applies
-// Q_panel^dagger to its 16-column tiles of the trailing matrix (W1 = V^dagger A,
-// W2 = T^dagger W1, A -= V W2) with register-blocked complex FMAs; a second
-// barrier precedes the next panel.  Conventions follow LAPACK's complex QR:
-// H_j = I - tau_j v_j v_j^dagger with v_j[j] = 1 implicit, R = H_K^dagger ...
-// H_1^dagger X, X = Q R, Q = H_1 ... H_K.  Every barrier wait is bounded.
+// Design (sm_103a): one persistent kernel launched as clusters of four CTAs.  Per panel of 32
+// columns, the four CTAs of cluster 0 factor the panel together (each holds 128 of its rows in
+// registers, four threads per row; the column sums of each step meet in distributed shared memory
+// after one cluster barrier) and CTA 0 forms the triangular factor T of the block reflector
+// Q_panel = I - V T V^dagger; after a grid barrier every CTA applies Q_panel^dagger to its
+// 16-column tiles of the trailing matrix (W1 = V^dagger A, W2 = T^dagger W1, A -= V W2) with
+// register-blocked complex FMAs; a second barrier precedes the next panel.  Conventions follow
+// LAPACK's complex QR: H_j = I - tau_j v_j v_j^dagger with v_j[j] = 1 implicit,
+// R = H_K^dagger ... H_1^dagger X, X = Q R, Q = H_1 ... H_K.  Every grid-barrier wait is bounded,
+// and the CTAs of cluster 0 agree on leaving after each one.
 #include <algorithm>
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -24,11 +26,16 @@ namespace eamps {
 
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kQrThreads = 512;
 constexpr int kQrPanel = 32;
 constexpr int kQrTile = 16;
 constexpr int kQrMaxRows = 512;
-constexpr int kQrPanelLd = kQrMaxRows + 1;   // padded column stride of the factored panel
+constexpr int kQrVs = kQrMaxRows * kQrPanel;      // reflector rows of one panel (shared memory)
+constexpr int kQrCluster = 4;                      // CTAs that factor each panel together
+constexpr int kQrMaxCtas = 16;                     // CTAs of one launch at most (one cluster)
+constexpr int kQrPanelRows = kQrMaxRows / kQrCluster;   // rows of the panel per CTA
 
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 // conj(a) * b
@@ -44,122 +51,208 @@ struct QrShared {
   float red[1];   // beta of the current reflector
 };
 
-// Factor the panel held column-major in pan (column j at pan + j * kQrPanelLd, rows 0..nr-1,
-// rows relative to the panel's first row) into jb reflectors; fills sh.tau and sh.T.
-// Per column j one transposed pass gives d_c = sum_{i > j} conj(x_i) A[i][c] for every column
-// c >= j at once (d_j is the squared norm below the diagonal); with v = x / (alpha - beta) the
-// reflector products are w_c = A[j][c] + conj(scale) d_c, so a column costs three barriers.
-// red2: 16 x 32 partial sums.  Loops are unrolled with two accumulators to keep shared-memory
-// loads in flight.
-__device__ void factor_panel(float2* pan, int nr, int jb, QrShared& sh, float2* red2) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  constexpr int NW = kQrThreads / 32;
-  for (int j = 0; j < jb; ++j) {
-    const float2* xj = pan + j * kQrPanelLd;
-    // partial d_c over this warp's 32 rows (lane = column c)
-    {
-      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-      const int i0 = max(warp * 32, j + 1), i1 = min(nr, warp * 32 + 32);
-      const float2* ac = pan + lane * kQrPanelLd;
-      if (lane >= j && lane < jb) {
-        int i = i0;
-#pragma unroll 4
-        for (; i + 1 < i1; i += 2) {
-          acc0 = c_add(acc0, c_mulc(xj[i], ac[i]));
-          acc1 = c_add(acc1, c_mulc(xj[i + 1], ac[i + 1]));
-        }
-        if (i < i1) acc0 = c_add(acc0, c_mulc(xj[i], ac[i]));
-      }
-      red2[warp * 32 + lane] = c_add(acc0, acc1);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      float2 dc = make_float2(0.f, 0.f);
+// The panel is factored by the kQrCluster CTAs of cluster 0: CTA r holds rows
+// [r * kQrPanelRows, (r + 1) * kQrPanelRows) of the panel, and each row is spread over four
+// threads of one warp (lane = 4 * row-in-warp + g), thread g holding columns [8 g, 8 g + 8) of the
+// row in registers.  Scratch layout (shared memory of each CTA): recv [2][kQrCluster][16 warps][32]
+// partial sums pushed by every warp of the cluster, by column parity; rowj [2][32] (row j of the
+// panel, pushed by CTA 0); then CTA 0's vg [32 x 32], vg[q * 32 + j] = (V^dagger V)[q][j] for
+// q < j, and M [32 x 32] for the merge of T.
+constexpr int kQrWarps = kQrThreads / 32;
+constexpr int kQrRecv = kQrCluster * kQrWarps * 32;
+constexpr int kQrRowjOff = 2 * kQrRecv;
+constexpr int kQrVgOff = kQrRowjOff + 64;
+constexpr int kQrMOff = kQrVgOff + kQrPanel * kQrPanel;
+static_assert(kQrPanelRows * 4 == kQrThreads, "four threads per panel row");
+static_assert(kQrMOff + kQrPanel * kQrPanel <= kQrVs, "panel scratch fits the reflector buffer");
+
+struct PanelCtx {
+  QrShared* sh;
+  float2* scratch;
+  int row, nr, jb, rank;
+};
+
+// Square root and reciprocal of a positive float from the hardware approximations plus one Newton
+// step (Heron's step for the root, r (2 - x r) for the reciprocal): within about an ulp, without
+// the out-of-line path of the IEEE operations, which sit on the panel's critical path.  Arguments
+// outside [1e-30, 1e30] take the IEEE operations.
+__device__ __forceinline__ float sqrt_nr(float x) {
+  if (!(x > 1e-30f && x < 1e30f)) return sqrtf(x);
+  const float y = rsqrtf(x), s = x * y;
+  return fmaf(0.5f * y, fmaf(-s, s, x), s);
+}
+__device__ __forceinline__ float rcp_nr(float x) {
+  const float ax = fabsf(x);
+  if (!(ax > 1e-30f && ax < 1e30f)) return 1.f / x;
+  const float r = __fdividef(1.f, x);
+  return r * fmaf(-x, r, 2.f);
+}
+
+// One halving round of a reduce-scatter over the lanes that differ in lane bit M: the lane keeps
+// the half of v[0, 2 O) selected by that bit, adds its partner's copy of it, and stores it in v[0, O).
+template <int O, int M>
+__device__ __forceinline__ void rs_round(float2 (&v)[8], int lane) {
+  const bool up = lane & M;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) dc = c_add(dc, red2[w * 32 + lane]);
-      const float xn2 = __shfl_sync(0xffffffffu, dc.x, j);
-      const float2 alpha = xj[j];
-      float2 tj = make_float2(0.f, 0.f), sc = make_float2(0.f, 0.f);
-      float beta = alpha.x;
-      if (!(xn2 == 0.f && alpha.y == 0.f)) {
-        const float an = sqrtf(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-        beta = (alpha.x >= 0.f) ? -an : an;
-        tj = make_float2((beta - alpha.x) / beta, -alpha.y / beta);
-        const float2 den = make_float2(alpha.x - beta, alpha.y);          // scale = 1 / (alpha - beta)
-        const float dd = den.x * den.x + den.y * den.y;
-        sc = make_float2(den.x / dd, -den.y / dd);
-      }
-      if (lane > j && lane < jb) sh.w[lane] = c_add(pan[lane * kQrPanelLd + j], c_mul(c_conj(sc), dc));
-      if (lane == 0) {
-        sh.tau[j] = tj;
-        sh.w[kQrPanel] = sc;
-        sh.red[0] = beta;
-      }
-    }
-    __syncthreads();
-    // v = x * scale below the diagonal, R[j][j] = beta, and A[i][c] -= conj(tau) v_i w_c
-    if (t >= j && t < nr) {
-      const float2 sc = sh.w[kQrPanel];
-      const float2 ctau = c_conj(sh.tau[j]);
-      float2* col = pan + j * kQrPanelLd;
-      float2 v;
-      if (t == j) {
-        v = make_float2(1.f, 0.f);
-        col[j] = make_float2(sh.red[0], 0.f);
-      } else {
-        v = c_mul(col[t], sc);
-        col[t] = v;
-      }
-      const float2 ctv = c_mul(ctau, v);
-#pragma unroll 4
-      for (int cc = j + 1; cc < jb; ++cc) {
-        float2* a = pan + cc * kQrPanelLd;
-        a[t] = c_sub(a[t], c_mul(ctv, sh.w[cc]));
-      }
-    }
-    __syncthreads();
+  for (int k = 0; k < O; ++k) {
+    const float2 send = up ? v[k] : v[k + O], keep = up ? v[k + O] : v[k];
+    v[k] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, M),
+                       keep.y + __shfl_xor_sync(0xffffffffu, send.y, M));
   }
-  // T (forward, columnwise): T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^dagger v_j)
-  for (int j = 0; j < jb; ++j) {
-    const float2* vj = pan + j * kQrPanelLd;
-    for (int p = warp; p < j; p += NW) {
-      const float2* vp = pan + p * kQrPanelLd;
-      float2 acc0 = (lane == 0) ? c_conj(vp[j]) : make_float2(0.f, 0.f);   // row j: v_j[j] = 1
-      float2 acc1 = make_float2(0.f, 0.f);
-      int i = j + 1 + lane;
-#pragma unroll 4
-      for (; i + 32 < nr; i += 64) {
-        acc0 = c_add(acc0, c_mulc(vp[i], vj[i]));
-        acc1 = c_add(acc1, c_mulc(vp[i + 32], vj[i + 32]));
-      }
-      if (i < nr) acc0 = c_add(acc0, c_mulc(vp[i], vj[i]));
-      float2 acc = c_add(acc0, acc1);
+}
+
+// Column step J of the panel.
+__device__ __forceinline__ void panel_step(float2 (&a)[8], const PanelCtx& p, cg::cluster_group& cl, const int J) {
+  QrShared& sh = *p.sh;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane & 3, par = J & 1;
+  float2* recv = p.scratch + par * kQrRecv;
+  float2* rowj = p.scratch + kQrRowjOff + par * 32;
+  // x = A[row][J], held by thread J / 8 of the row
+  const bool b0 = J & 1, b1 = J & 2, b2 = J & 4;   // a[J & 7] by a tree of selects
+  const float2 m01 = b0 ? a[1] : a[0], m23 = b0 ? a[3] : a[2], m45 = b0 ? a[5] : a[4], m67 = b0 ? a[7] : a[6];
+  const float2 m03 = b1 ? m23 : m01, m47 = b1 ? m67 : m45;
+  const float2 mine = b2 ? m47 : m03;
+  const int src = (lane & ~3) | (J >> 3);
+  const float2 x = make_float2(__shfl_sync(0xffffffffu, mine.x, src), __shfl_sync(0xffffffffu, mine.y, src));
+  if (p.rank == 0 && p.row == J) {   // row J of the panel (CTA 0) to every CTA
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (lane == 0) sh.w[p] = acc;
+    for (int r = 0; r < kQrCluster; ++r) {
+      float2* dst = cl.map_shared_rank(rowj, r) + 8 * g;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dst[k] = a[k];
     }
-    __syncthreads();
-    if (t < j) {
-      float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-      int q = t;
-#pragma unroll 4
-      for (; q + 1 < j; q += 2) {
-        acc0 = c_add(acc0, c_mul(sh.T[t * kQrPanel + q], sh.w[q]));
-        acc1 = c_add(acc1, c_mul(sh.T[t * kQrPanel + q + 1], sh.w[q + 1]));
-      }
-      if (q < j) acc0 = c_add(acc0, c_mul(sh.T[t * kQrPanel + q], sh.w[q]));
-      const float2 v = c_mul(sh.tau[j], c_add(acc0, acc1));
-      sh.T[t * kQrPanel + j] = make_float2(-v.x, -v.y);
-    } else if (t == j) {
-      sh.T[j * kQrPanel + j] = sh.tau[j];
-    } else if (t < kQrPanel) {
-      sh.T[t * kQrPanel + j] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
   }
+  // slot s = 8 g + k: d_s = sum conj(x) A[.][s] for s >= J, y_s = sum conj(V[.][s]) x for s < J,
+  // over the rows below J; summed over the warp's 8 rows by a reduce-scatter over lane bits 4, 3, 2
+  const float2 xm = (p.row > J && p.row < p.nr) ? x : make_float2(0.f, 0.f);
+  float2 v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (8 * g + k >= J) ? c_mulc(xm, a[k]) : c_mulc(a[k], xm);
+  rs_round<4, 16>(v, lane);
+  rs_round<2, 8>(v, lane);
+  rs_round<1, 4>(v, lane);
+  // this lane now holds the warp's sum of slot 8 g + (lane >> 2): push it to every CTA
+  const int slot = 8 * g + (lane >> 2);
+#pragma unroll
+  for (int r = 0; r < kQrCluster; ++r) cl.map_shared_rank(recv, r)[(p.rank * kQrWarps + warp) * 32 + slot] = v[0];
+  cl.sync();
+  if (warp == 0) {   // every CTA forms the same scalars from the same sums, in the same order
+    float2 d4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll 16
+    for (int e = 0; e < kQrCluster * kQrWarps; ++e) d4[e & 3] = c_add(d4[e & 3], recv[e * 32 + lane]);
+    const float2 dc = c_add(c_add(d4[0], d4[1]), c_add(d4[2], d4[3]));
+    const float xn2 = __shfl_sync(0xffffffffu, dc.x, J);
+    const float2 alpha = rowj[J];
+    const float2 rl = rowj[lane];
+    float2 sc = make_float2(0.f, 0.f), tj = make_float2(0.f, 0.f);
+    float beta = alpha.x;
+    if (!(xn2 == 0.f && alpha.y == 0.f)) {
+      const float an = sqrt_nr(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+      beta = (alpha.x >= 0.f) ? -an : an;
+      const float ib = rcp_nr(beta);
+      tj = make_float2((beta - alpha.x) * ib, -alpha.y * ib);
+      const float2 den = make_float2(alpha.x - beta, alpha.y);          // scale = 1 / (alpha - beta)
+      const float idd = rcp_nr(den.x * den.x + den.y * den.y);
+      sc = make_float2(den.x * idd, -den.y * idd);
+    }
+    sh.w[lane] = (lane > J && lane < p.jb) ? c_add(rl, c_mul(c_conj(sc), dc)) : make_float2(0.f, 0.f);
+    if (p.rank == 0 && lane < J) p.scratch[kQrVgOff + lane * 32 + J] = c_add(c_mul(sc, dc), c_conj(rl));
+    if (lane == 0) {
+      sh.tau[J] = tj;
+      sh.w[kQrPanel] = sc;
+      sh.red[0] = beta;
+    }
+  }
+  __syncthreads();
+  // v = x * scale below the diagonal, R[J][J] = beta, and A[i][c] -= conj(tau) v_i w_c (w_c = 0
+  // for c <= J, so those entries keep their values; entry J then takes v or beta)
+  if (p.row >= J && p.row < p.nr) {
+    const float2 sc = sh.w[kQrPanel];
+    const float2 ctau = c_conj(sh.tau[J]);
+    const bool diag = p.row == J;
+    const float2 vv = diag ? make_float2(1.f, 0.f) : c_mul(x, sc);
+    const float2 nj = diag ? make_float2(sh.red[0], 0.f) : vv;
+    const float2 ctv = c_mul(ctau, vv);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 u = c_sub(a[k], c_mul(ctv, sh.w[8 * g + k]));
+      a[k] = (8 * g + k == J) ? nj : u;
+    }
+  }
+}
+
+// Factor the panel of rows r0.., columns c0.. of X (nr <= 512 rows, jb <= 32 columns) in place
+// into jb reflectors (LAPACK layout: R on and above the diagonal, v below it, v_j[j] = 1
+// implicit), run by the CTAs of cluster 0; CTA 0 also fills sh.tau and sh.T.  The rows stay in
+// registers for the whole factorisation, so a column step moves no panel data.  Step j needs,
+// over the rows i > j, d_c = sum_i conj(x_i) A[i][c] for the columns c >= j (d_j = squared norm
+// below the diagonal, x = column j) and, for the compact-WY factor, y_q = sum_i conj(V[i][q]) x_i
+// for the earlier reflectors q < j: together exactly 32 sums, reduced within each warp, pushed to
+// every CTA of the cluster through distributed shared memory and summed there after one cluster
+// barrier.  With v = x / (alpha - beta) the reflector products are w_c = A[j][c] + conj(scale) d_c,
+// and (V^dagger v_j)_q = scale y_q + conj(V[j][q]).  After the last column CTA 0 builds T by
+// merging blocks of reflectors: for adjacent blocks 1, 2 of size b,
+// T = [[T1, -T1 (V1^dagger V2) T2], [0, T2]], five levels from the single reflectors (T = tau).
+// scratch: the reflector buffer of this CTA's shared memory, unused otherwise during the panel.
+__device__ void factor_panel(float2* X, long long ldx, int r0, int c0, int nr, int jb, QrShared& sh, float2* scratch,
+                             cg::cluster_group& cl) {
+  const int t = threadIdx.x, rank = (int)cl.block_rank(), g = t & 3;
+  PanelCtx p;
+  p.sh = &sh;
+  p.scratch = scratch;
+  float2* vg = scratch + kQrVgOff;
+  float2* M = scratch + kQrMOff;   // CTA 0: products of the merge
+  p.row = rank * kQrPanelRows + (t >> 2);
+  p.nr = nr;
+  p.jb = jb;
+  p.rank = rank;
+  float2 a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    a[k] = (p.row < nr && 8 * g + k < jb) ? __ldcg(X + (long long)(c0 + 8 * g + k) * ldx + r0 + p.row)
+                                          : make_float2(0.f, 0.f);
+  if (rank == 0)
+    for (int e = t; e < kQrPanel * kQrPanel; e += kQrThreads) vg[e] = make_float2(0.f, 0.f);
+  cl.sync();   // every CTA of the cluster is running before remote stores (and vg is clear)
+#pragma unroll 1
+  for (int j = 0; j < jb; ++j) panel_step(a, p, cl, j);   // (jb is the same for the whole cluster)
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (p.row < nr && 8 * g + k < jb) __stcg(X + (long long)(c0 + 8 * g + k) * ldx + r0 + p.row, a[k]);
+  if (rank == 0) {
+    // T by merging: leaves T[i][i] = tau_i (0 past jb), then levels b = 1, 2, 4, 8, 16
+    for (int e = t; e < kQrPanel * kQrPanel; e += kQrThreads) {
+      const int i = e >> 5, j = e & 31;
+      sh.T[e] = (i == j && i < jb) ? sh.tau[i] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int b = 1; b < kQrPanel; b *= 2) {
+      const int n = (kQrPanel / (2 * b)) * b * b;   // entries of all the blocks T12 of this level
+      for (int e = t; e < n; e += kQrThreads) {     // M = V1^dagger V2 T2
+        const int blk = e / (b * b), i = (e / b) % b, j = e % b, o = 2 * b * blk;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k = 0; k <= j; ++k)
+          acc = c_add(acc, c_mul(vg[(o + i) * 32 + o + b + k], sh.T[(o + b + k) * kQrPanel + o + b + j]));
+        M[(o + i) * 32 + o + b + j] = acc;
+      }
+      __syncthreads();
+      for (int e = t; e < n; e += kQrThreads) {     // T12 = -T1 M
+        const int blk = e / (b * b), i = (e / b) % b, j = e % b, o = 2 * b * blk;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k = i; k < b; ++k)
+          acc = c_add(acc, c_mul(sh.T[(o + i) * kQrPanel + o + k], M[(o + k) * 32 + o + b + j]));
+        sh.T[(o + i) * kQrPanel + o + b + j] = make_float2(-acc.x, -acc.y);
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+}
+
+// The cluster barriers of factor_panel, for the CTAs of the cluster that do not factor the panel.
+__device__ __forceinline__ void panel_idle(cg::cluster_group& cl, int jb) {
+  cl.sync();
+  for (int j = 0; j < jb; ++j) cl.sync();
 }
 
 // Copy a rows x cols block (column-major) global -> shared with eight loads in flight per thread.
@@ -301,44 +394,45 @@ struct QrArgs {
   DevCtrl* ctrl;
 };
 
+// Both kernels run as ONE thread-block cluster (the whole grid): the hardware schedules its CTAs
+// together, so the steps are separated by cluster barriers and nothing spins on memory.
 __global__ void __launch_bounds__(kQrThreads, 1) qr_factor_kernel(QrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ QrShared sh;
-  float2* big = reinterpret_cast<float2*>(smem_raw);   // panel (CTA 0, 32 x 513) or reflector rows (512 x 32)
-  float2* At = big + kQrPanel * kQrPanelLd;            // staged tile, 16 x 512
+  float2* big = reinterpret_cast<float2*>(smem_raw);   // panel scratch (ranks < kQrCluster) or reflector rows
+  float2* At = big + kQrVs;                            // staged tile, 16 x 512
   float2* As = At + kQrMaxRows * kQrTile;              // 4 x 16 x 32
   float2* W = As + 4 * kQrTile * kQrPanel;             // 16 x 32
-  const int P = gridDim.x;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), P = (int)cl.num_blocks();
   const int K = min(a.l, a.c);
   const int npan = (K + kQrPanel - 1) / kQrPanel;
   for (int k = 0; k < npan; ++k) {
     const int c0 = k * kQrPanel, jb = min(kQrPanel, K - c0), r0 = c0, nr = a.l - r0;
-    if (blockIdx.x == 0) {
-      load2d(big, kQrPanelLd, a.X + (long long)c0 * a.ldx + r0, a.ldx, nr, jb);
-      __syncthreads();
-      factor_panel(big, nr, jb, sh, W);
-      for (int e = threadIdx.x; e < jb * nr; e += kQrThreads) {
-        const int j = e / nr, i = e % nr;
-        __stcg(a.X + (long long)(c0 + j) * a.ldx + r0 + i, big[j * kQrPanelLd + i]);
+    if (rank < kQrCluster) {   // ranks 0..3 factor the panel
+      factor_panel(a.X, a.ldx, r0, c0, nr, jb, sh, big, cl);
+      if (rank == 0) {
+        for (int e = threadIdx.x; e < kQrPanel * kQrPanel; e += kQrThreads) a.Tm[(long long)k * kQrPanel * kQrPanel + e] = sh.T[e];
+        if (threadIdx.x < jb) a.tau[c0 + threadIdx.x] = sh.tau[threadIdx.x];
       }
-      for (int e = threadIdx.x; e < kQrPanel * kQrPanel; e += kQrThreads) a.Tm[(long long)k * kQrPanel * kQrPanel + e] = sh.T[e];
-      if (threadIdx.x < jb) a.tau[c0 + threadIdx.x] = sh.tau[threadIdx.x];
       __threadfence();
+    } else {
+      panel_idle(cl, jb);   // the same cluster barriers as factor_panel
     }
     const int first = c0 + jb;   // trailing columns
     if (first >= a.c) break;
-    if (!grid_barrier(a.ctrl, P)) return;
+    cl.sync();
     // every CTA: V and T of this panel, then its tiles
     load_v(a.X, a.ldx, r0, nr, c0, jb, big);
     for (int e = threadIdx.x; e < kQrPanel * kQrPanel; e += kQrThreads) sh.T[e] = __ldcg(a.Tm + (long long)k * kQrPanel * kQrPanel + e);
     __syncthreads();
     const int ntiles = (a.c - first + kQrTile - 1) / kQrTile;
-    for (int tile = blockIdx.x; tile < ntiles; tile += P) {
+    for (int tile = rank; tile < ntiles; tile += P) {
       const int tc = first + tile * kQrTile, tw = min(kQrTile, a.c - tc);
       apply_block(a.X + (long long)tc * a.ldx + r0, a.ldx, nr, tw, jb, big, sh.T, true, At, As, W);
     }
     __threadfence();
-    if (!grid_barrier(a.ctrl, P)) return;
+    cl.sync();
   }
 }
 
@@ -347,20 +441,21 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_form_q_kernel(QrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ QrShared sh;
   float2* big = reinterpret_cast<float2*>(smem_raw);
-  float2* At = big + kQrPanel * kQrPanelLd;
+  float2* At = big + kQrVs;
   float2* As = At + kQrMaxRows * kQrTile;
   float2* W = As + 4 * kQrTile * kQrPanel;
-  const int P = gridDim.x;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), P = (int)cl.num_blocks();
   const int K = min(a.l, a.c);
   const int npan = (K + kQrPanel - 1) / kQrPanel;
   // Q = [I; 0]
   const long long total = (long long)a.kq * a.l;
-  for (long long e = blockIdx.x * (long long)kQrThreads + threadIdx.x; e < total; e += (long long)P * kQrThreads) {
+  for (long long e = rank * (long long)kQrThreads + threadIdx.x; e < total; e += (long long)P * kQrThreads) {
     const int col = (int)(e / a.l), row = (int)(e % a.l);
     a.Q[(long long)col * a.ldq + row] = make_float2(row == col ? 1.f : 0.f, 0.f);
   }
   __threadfence();
-  if (!grid_barrier(a.ctrl, P)) return;
+  cl.sync();
   for (int k = npan - 1; k >= 0; --k) {
     const int c0 = k * kQrPanel, jb = min(kQrPanel, K - c0), r0 = c0, nr = a.l - r0;
     load_v(a.X, a.ldx, r0, nr, c0, jb, big);
@@ -368,50 +463,90 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_form_q_kernel(QrArgs a) {
     __syncthreads();
     // columns < c0 of Q are still unit vectors above row c0: untouched by this panel
     const int ntiles = (a.kq - c0 + kQrTile - 1) / kQrTile;
-    for (int tile = blockIdx.x; tile < ntiles; tile += P) {
+    for (int tile = rank; tile < ntiles; tile += P) {
       const int tc = c0 + tile * kQrTile, tw = min(kQrTile, a.kq - tc);
       apply_block(a.Q + (long long)tc * a.ldq + r0, a.ldq, nr, tw, jb, big, sh.T, false, At, As, W);
     }
     __threadfence();
-    if (!grid_barrier(a.ctrl, P)) return;
+    cl.sync();
   }
 }
 
 size_t qr_smem_bytes() {
-  return sizeof(float2) * ((size_t)kQrPanel * kQrPanelLd + (size_t)kQrMaxRows * kQrTile + 4 * kQrTile * kQrPanel +
+  return sizeof(float2) * ((size_t)kQrVs + (size_t)kQrMaxRows * kQrTile + 4 * kQrTile * kQrPanel +
                             kQrTile * kQrPanel);
 }
 
-cudaError_t launch_qr(const void* fn, QrArgs& a, int ctas, cudaStream_t st) {
+cudaError_t set_qr_attrs(const void* fn) {
   cudaError_t e = allow_dynamic_smem(fn);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// One cluster of `ctas` CTAs (kQrCluster .. kQrMaxCtas): the whole grid.
+cudaError_t launch_qr(const void* fn, QrArgs& a, int ctas, cudaStream_t st) {
+  cudaError_t e = set_qr_attrs(fn);
   if (e != cudaSuccess) return e;
-  // reset the barrier counters (bar_count, bar_gen, rot[3] are contiguous)
-  e = cudaMemsetAsync(&a.ctrl->bar_count, 0, 5 * sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
+  ctas = std::max(kQrCluster, std::min(ctas, kQrMaxCtas));
   void* args[] = {&a};
-  const size_t smem = qr_smem_bytes();
-  if (ctas <= 1) return cudaLaunchKernel(fn, dim3(1), dim3(kQrThreads), args, smem, st);
-  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kQrThreads), args, smem, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(kQrThreads);
+  cfg.dynamicSmemBytes = qr_smem_bytes();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace
 
 int qr_max_rows() { return kQrMaxRows; }
 
+// CTAs of one launch (one cluster): one per 16-column tile, at least kQrCluster, at most max_ctas.
 int qr_ctas(int l, int c, int max_ctas) {
+  (void)l;
   const int tiles = (c + kQrTile - 1) / kQrTile;
-  return std::max(1, std::min(tiles, max_ctas));
+  return std::max(kQrCluster, std::min(tiles, std::min(max_ctas, kQrMaxCtas)));
 }
 
+// The largest cluster of both kernels that the device can hold (kQrMaxCtas, 8 or kQrCluster CTAs;
+// 0 if none).
 int qr_max_ctas() {
-  int per_sm = 0, dev = 0, sms = 0;
-  if (allow_dynamic_smem((const void*)qr_factor_kernel) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_factor_kernel, kQrThreads, qr_smem_bytes()) !=
-      cudaSuccess)
-    return 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return per_sm * sms;
+  const void* fns[2] = {(const void*)qr_factor_kernel, (const void*)qr_form_q_kernel};
+  for (const void* fn : fns)
+    if (set_qr_attrs(fn) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+  for (int n : {kQrMaxCtas, 8, kQrCluster}) {
+    bool fits = true;
+    for (const void* fn : fns) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)n);
+      cfg.blockDim = dim3(kQrThreads);
+      cfg.dynamicSmemBytes = qr_smem_bytes();
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)n;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        fits = false;
+      }
+    }
+    if (fits) return n;
+  }
+  return 0;
 }
 
 cudaError_t qr_factor(float2* X, long long ldx, int l, int c, float2* tau, float2* Tm, DevCtrl* ctrl, int ctas,
