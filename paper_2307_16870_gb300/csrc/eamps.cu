@@ -199,6 +199,15 @@ namespace {
 template <class R>
 struct Engine final : mps_state {
   using Z = cplx<R>;
+  // Centre moves by QR: forming the explicit Q and writing the site from it run on a second
+  // stream, beside the next gate (which does not touch that site; a handle that runs alone only).
+  // Every later user of the QR buffers or of the sites first makes the handle's stream wait for
+  // that work (join_side).
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_side = nullptr;
+  Z* Xq = nullptr;      // the move's matrix, factored in place (R above the diagonal, reflectors below)
+  Z* Qq = nullptr;      // its explicit Q
+  bool side_pending = false;
   mps_options opt{};
   int sm_count = 1;
   int chi_cap = kDefaultCap;
@@ -249,17 +258,21 @@ struct Engine final : mps_state {
 
   ~Engine() override {
     for (Engine* h : helpers) delete h;
+    if (side) cudaStreamSynchronize(side);
     if (stream) cudaStreamSynchronize(stream);
     coop_release();
     if (!lam_owned) lam = nullptr;
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
-                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T, lam};
+                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T, lam, Xq, Qq};
     for (void* b : bufs) if (b) cudaFree(b);
     if (hctrl) cudaFreeHost(hctrl);
     if (hout) cudaFreeHost(hout);
     if (tc) tc_destroy(tc);
     for (auto& t : pending) { ev_pool.push_back(t.a); ev_pool.push_back(t.b); }
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (ev_main) cudaEventDestroy(ev_main);
+    if (ev_side) cudaEventDestroy(ev_side);
+    if (side) cudaStreamDestroy(side);
     if (owns_stream && stream) cudaStreamDestroy(stream);
   }
 
@@ -286,18 +299,25 @@ struct Engine final : mps_state {
     cudaEventCreate(&e);
     return e;
   }
-  // start an event-timed region (kind 0 = Jacobi, 1 = contraction) on the handle's stream
-  int tbegin() {
+  // start an event-timed region (kind 0 = Jacobi, 1 = contraction, 2 = Jacobi of a move, 3 = QR)
+  // on the handle's stream (or on `on`)
+  int tbegin(cudaStream_t on = nullptr) {
     if (!prof) return -1;
     Timed t{ev_get(), ev_get(), 0};
-    cudaEventRecord(t.a, stream);
+    cudaEventRecord(t.a, on ? on : stream);
     pending.push_back(t);
     return (int)pending.size() - 1;
   }
-  void tend(int id, int kind) {
+  void tend(int id, int kind, cudaStream_t on = nullptr) {
     if (id < 0) return;
     pending[id].kind = kind;
-    cudaEventRecord(pending[id].b, stream);
+    cudaEventRecord(pending[id].b, on ? on : stream);
+  }
+  // the handle's stream waits for the work of the move's second stream
+  mps_status join_side() {
+    if (!side_pending) return MPS_OK;
+    side_pending = false;
+    return cu(cudaStreamWaitEvent(stream, ev_side, 0));
   }
   // after a stream synchronisation: harvest the event durations
   void harvest() {
@@ -431,6 +451,14 @@ struct Engine final : mps_state {
       if (qr_fit <= 0) qr_on = false;
       if (qr_on && (!dalloc(&qr_tau, (size_t)c_max) || !dalloc(&qr_T, (size_t)1024 * ((c_max + 31) / 32))))
         return MPS_ERR_OOM;
+      if (qr_on && (qr_mode & 2)) {
+        if (!dalloc(&Xq, (size_t)qr_max_rows() * c_max) || !dalloc(&Qq, (size_t)qr_max_rows() * qr_max_rows()))
+          return MPS_ERR_OOM;
+        if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming) != cudaSuccess)
+          return MPS_ERR_CUDA;
+      }
     }
     return MPS_OK;
   }
@@ -537,6 +565,7 @@ struct Engine final : mps_state {
   }
 
   mps_status svd_tune(int l, int c, int acc, int* layout) override {
+    if (mps_status js = join_side()) return js;
     if (l < 1 || c < 1 || l > c_max || c > c_max) return MPS_ERR_ARG;
     if (mps_status s = sync()) return s;
     const int kind = layout_for(l, c, acc != 0, true);
@@ -571,6 +600,7 @@ struct Engine final : mps_state {
   // X (l x c, column-major, ld ldx) = Q R in place; with Q != nullptr also the explicit Q
   // (l x min(l, c), column-major, ld ldq).
   mps_status qr_run(int l, int c, Z* Xp, long long ldx, Z* Q, long long ldq) {
+    if (mps_status s = join_side()) return s;   // qr_T and qr_tau may still be read there
     if constexpr (std::is_same<R, float>::value) {
       const int ctas = qr_ctas(l, c, qr_fit);   // one cluster: no co-residency budget needed
       ++n_qr;
@@ -585,6 +615,28 @@ struct Engine final : mps_state {
     }
   }
 
+  // The explicit Q (l x min(l, c), ld l, into Qq) of the move's matrix QX just factored on the
+  // handle's stream, then the site write-back out <- Qq (the extract of the plain path), both on
+  // the second stream; the handle's stream goes on with the next steps.
+  mps_status side_q(int l, int c, const Z* QX, Z* out, long long o_js, long long o_rs, int kout, int rows,
+                    int conj) {
+    if constexpr (std::is_same<R, float>::value) {
+      if (mps_status s = cu(cudaEventRecord(ev_main, stream))) return s;
+      if (mps_status s = cu(cudaStreamWaitEvent(side, ev_main, 0))) return s;
+      const int id = tbegin(side);
+      mps_status s = kl(qr_form_q(QX, l, l, c, qr_T, Qq, l, ctrl, qr_ctas(l, std::min(l, c), qr_fit), side));
+      tend(id, 3, side);
+      if (s == MPS_OK)
+        s = kl(extract_columns<R>(out, o_js, o_rs, kout, rows, Qq, l, 1, nullptr, conj, nullptr, 0, ctrl, side));
+      if (s == MPS_OK) s = cu(cudaEventRecord(ev_side, side));
+      if (s == MPS_OK) side_pending = true;
+      return s;
+    } else {
+      (void)l; (void)c; (void)QX; (void)out; (void)o_js; (void)o_rs; (void)kout; (void)rows; (void)conj;
+      return MPS_ERR_ARG;
+    }
+  }
+
   // Vidal form of a product state: every bond of dimension 1 with Schmidt value 1
   mps_status reset_lambda() {
     std::vector<double> h((size_t)(N + 1) * lam_stride, 0.0);
@@ -595,6 +647,7 @@ struct Engine final : mps_state {
   }
 
   mps_status read_ctrl() {
+    if (mps_status s = join_side()) return s;
     if (mps_status s = cu(cudaMemcpyAsync(hctrl, ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, stream))) return s;
     if (mps_status s = cu(cudaStreamSynchronize(stream))) return s;
     coop_release();   // every launch of this handle has finished
@@ -616,12 +669,16 @@ struct Engine final : mps_state {
     if ((qr_mode & 2) && qr_ok(m, n)) {
       // C (m x n) = Q R: A_c <- Q (m x K), A_{c+1} <- R A_{c+1} (K x n2), bond K = min(m, n)
       const int K = std::min(m, n);
-      if ((s = extract(X, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;       // X = C column-major
-      if ((s = qr_run(m, n, X, m, Wacc, m))) return s;                                     // Q column-major
-      if ((s = kl(triu_extract<R>(tmp2, n, 1, X, m, K, n, 0, stream)))) return s;           // R row-major K x n
+      const bool ovl = side && !shared_gpu;   // Q and the write-back of A_c beside the next steps
+      Z* QX = ovl ? Xq : X;
+      if ((s = join_side())) return s;
+      if ((s = extract(QX, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;      // QX = C column-major
+      if ((s = qr_run(m, n, QX, m, ovl ? nullptr : Wacc, m))) return s;                   // Q column-major
+      if (ovl && (s = side_q(m, n, QX, C, 1, K, K, m, 0))) return s;                      // A_c = Q row-major
+      if ((s = kl(triu_extract<R>(tmp2, n, 1, QX, m, K, n, 0, stream)))) return s;         // R row-major K x n
       if ((s = gemm(K, n2, n, R(1), tmp2, n, 1, 0, Nx, n2, 1, 0, T, n2, 1))) return s;     // R A_{c+1}
       if ((s = copy(Nx, T, (size_t)K * n2))) return s;
-      if ((s = extract(C, 1, K, K, m, Wacc, m, 1, nullptr, 0, nullptr, 0))) return s;      // A_c = Q row-major
+      if (!ovl && (s = extract(C, 1, K, K, m, Wacc, m, 1, nullptr, 0, nullptr, 0))) return s;   // A_c = Q row-major
       bonds[c + 1] = K;
     } else if (n <= m) {
       // X = C column-major; C W = Y; Q = Y/|Y| (m x n), R = Q^dagger C, A_{c+1} <- R A_{c+1}
@@ -659,13 +716,17 @@ struct Engine final : mps_state {
       // C^dagger (n x m) = Q R, so C = R^dagger Q^dagger: A_c <- Q^dagger (K x n),
       // A_{c-1} <- A_{c-1} R^dagger (m2 x K), bond K = min(m, n)
       const int K = std::min(m, n);
-      if ((s = extract(X, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;        // X = C^dagger
-      if ((s = qr_run(n, m, X, n, Wacc, n))) return s;                                     // Q column-major n x K
-      if ((s = kl(triu_extract<R>(tmp2, m, 1, X, n, K, m, 0, stream)))) return s;           // R row-major K x m
+      const bool ovl = side && !shared_gpu;   // Q and the write-back of A_c beside the next steps
+      Z* QX = ovl ? Xq : X;
+      if ((s = join_side())) return s;
+      if ((s = extract(QX, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;       // QX = C^dagger
+      if ((s = qr_run(n, m, QX, n, ovl ? nullptr : Wacc, n))) return s;                   // Q column-major n x K
+      // Q^dagger row-major (K x n): element (r, j) = conj(Q(j, r)) sits where Q(j, r) sits
+      if (ovl && (s = side_q(n, m, QX, C, n, 1, K, n, 1))) return s;
+      if ((s = kl(triu_extract<R>(tmp2, m, 1, QX, n, K, m, 0, stream)))) return s;         // R row-major K x m
       if ((s = gemm(m2, K, m, R(1), Pv, m, 1, 0, tmp2, 1, m, 1, T, K, 1))) return s;       // A_{c-1} R^dagger
       if ((s = copy(Pv, T, (size_t)m2 * K))) return s;
-      // Q^dagger row-major (K x n): element (r, j) = conj(Q(j, r)) sits where Q(j, r) sits
-      if ((s = extract(C, n, 1, K, n, Wacc, n, 1, nullptr, 1, nullptr, 0))) return s;
+      if (!ovl && (s = extract(C, n, 1, K, n, Wacc, n, 1, nullptr, 1, nullptr, 0))) return s;
       bonds[c] = K;
     } else if (m <= n) {
       // X = C^dagger; C^dagger W = Y -> C = (W S) Yn^dagger: Q' = Yn^dagger (m x n), L = C Q'^dagger
@@ -725,6 +786,7 @@ struct Engine final : mps_state {
   }
 
   mps_status apply_1q(int q, const double* op, int op_dim) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (q < 0 || q >= N || !op) return MPS_ERR_ARG;
     std::vector<double> g;
@@ -741,6 +803,7 @@ struct Engine final : mps_state {
 
   // The hot path of the entanglement-aware algorithm for one two-qubit gate.
   mps_status apply_2q(int q, const double* op, bool on_device, int op_dim, double target) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (q < 0 || q + 1 >= N || !op) return MPS_ERR_ARG;
     const int D2 = d * d;
@@ -858,6 +921,7 @@ struct Engine final : mps_state {
   // schedule's value for the product at the layer's start.
   mps_status apply_layer(int n, const int* qs, const double* ops_dev, int op_dim, double target,
                          int concurrency) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (!vidal) return MPS_ERR_STATE;
     if (n < 0 || (n > 0 && (!qs || !ops_dev)) || concurrency < 1 || op_dim != 4) return MPS_ERR_ARG;
@@ -943,6 +1007,7 @@ struct Engine final : mps_state {
 
   mps_status gemm_device(int M, int Nn, int K, const void* A, long long a_rs, long long a_cs, int cA, const void* B,
                          long long b_rs, long long b_cs, int cB, void* C, long long c_rs, long long c_cs) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (M < 1 || Nn < 1 || K < 1 || !A || !B || !C) return MPS_ERR_ARG;
     return gemm(M, Nn, K, R(1), (const Z*)A, a_rs, a_cs, cA, (const Z*)B, b_rs, b_cs, cB, (Z*)C, c_rs, c_cs);
@@ -953,6 +1018,7 @@ struct Engine final : mps_state {
   // Aq = U_k (m x k), Ap = U_k^H A / sqrt(W_k) (k x n).  out4 (host) = {k, W_k/W, W, W_k}.
   mps_status tsvd_device(int m, int n, const void* Av, long long lda, double target, int max_k, double rank_tol,
                          void* Uv, double* S, void* Vv, void* Aqv, void* Apv, double* out4) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (m < 1 || n < 1 || !Av || lda < n || !Uv || !S || !Vv || !Aqv || !Apv || !out4 || !(target >= 0.0) ||
         !(rank_tol >= 0.0))
@@ -1008,6 +1074,7 @@ struct Engine final : mps_state {
   // Reverse-mode derivative of tsvd_device's (Aq, Ap) with respect to A (see tsvd_grad.cu)
   mps_status tsvd_backward_device(int m, int n, int k, const void* Uv, const double* S, const void* Vv,
                                   const void* Aq_bar, const void* Ap_bar, double eps, void* A_bar) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     const int c = std::min(m, n);
     if (m < 1 || n < 1 || k < 1 || k > c || !Uv || !S || !Vv || !A_bar || !(eps >= 0.0)) return MPS_ERR_ARG;
@@ -1047,6 +1114,7 @@ struct Engine final : mps_state {
   // failure detection: a bounded wait whose signal never comes gives up at the handle's deadline,
   // and the status word carries the timeout to the host (see mps_selftest_timeout)
   mps_status selftest_timeout(int site, long long wait_ns) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (site < MPS_SELFTEST_FLAG || site > MPS_SELFTEST_GEMM || wait_ns < 1000 || wait_ns > 20000000000LL)
       return MPS_ERR_ARG;
@@ -1117,6 +1185,7 @@ struct Engine final : mps_state {
   bool is_vidal() const override { return vidal; }
 
   mps_status site_to_double(int i, double2* dst, cudaStream_t st) override {
+    if (mps_status js = join_side()) return js;
     if (i < 0 || i >= N || !dst) return MPS_ERR_ARG;
     return kl(to_double<R>(site[i], dst, (long long)bonds[i] * d * bonds[i + 1], st));
   }
@@ -1130,6 +1199,7 @@ struct Engine final : mps_state {
   mps_status sync() override { return read_ctrl(); }
 
   mps_status reset() override {
+    if (mps_status js = join_side()) return js;
     mps_status s;
     if ((s = cu(cudaStreamSynchronize(stream)))) return s;
     fold_helper_stats();
@@ -1162,6 +1232,7 @@ struct Engine final : mps_state {
   }
 
   mps_status profile(int on) override {
+    if (mps_status js = join_side()) return js;
     prof = on != 0;
     return MPS_OK;
   }
@@ -1195,6 +1266,7 @@ struct Engine final : mps_state {
 
   // gates run on helper handles count once, as gates of this handle
   mps_status stats(mps_stats_t* out) override {
+    if (mps_status js = join_side()) return js;
     mps_status s = read_ctrl();
     out->kernel_launches = n_launch;
     out->jacobi_launches = n_jac;
@@ -1219,6 +1291,7 @@ struct Engine final : mps_state {
   }
 
   mps_status stats_reset() override {
+    if (mps_status js = join_side()) return js;
     mps_status s;
     if ((s = cu(cudaStreamSynchronize(stream)))) return s;
     harvest();
@@ -1258,6 +1331,7 @@ struct Engine final : mps_state {
   }
 
   mps_status expect(int q, int support, const double* op, double* out) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (vidal) return MPS_ERR_STATE;   // the local formula needs a canonical centre on the support
     if (!op || !out || (support != 1 && support != 2) || q < 0 || q + support > N) return MPS_ERR_ARG;
@@ -1310,6 +1384,7 @@ struct Engine final : mps_state {
   }
 
   mps_status amplitude(const unsigned char* bits, double* out) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (!bits || !out) return MPS_ERR_ARG;
     std::vector<double2> w((size_t)N * d, make_double2(0, 0));
@@ -1334,6 +1409,7 @@ struct Engine final : mps_state {
   }
 
   mps_status get_site(int i, double* out, long long capd, int* dims3) override {
+    if (mps_status js = join_side()) return js;
     if (i < 0 || i >= N || !out || !dims3) return MPS_ERR_ARG;
     const long long count = (long long)bonds[i] * d * bonds[i + 1];
     dims3[0] = bonds[i]; dims3[1] = d; dims3[2] = bonds[i + 1];
@@ -1345,6 +1421,7 @@ struct Engine final : mps_state {
   }
 
   mps_status set_site(int i, const double* data, const int* dims3) override {
+    if (mps_status js = join_side()) return js;
     if (sticky) return from_bits(sticky);
     if (vidal) return MPS_ERR_STATE;   // the Schmidt vectors would no longer match the sites
     if (i < 0 || i >= N || !data || !dims3) return MPS_ERR_ARG;
@@ -1362,6 +1439,7 @@ struct Engine final : mps_state {
   }
 
   mps_status last_svals(double* out, int capn, int* count) override {
+    if (mps_status js = join_side()) return js;
     if (!out || !count) return MPS_ERR_ARG;
     const int nwr = std::min(capn, last_c);
     *count = nwr;
