@@ -57,6 +57,9 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
     ap.add_argument("--svd-kernel", default="auto", choices=["auto", "tournament", "gram"],
                     help="layout of the Jacobi SVD (mps_options.svd_kernel)")
+    ap.add_argument("--qr", default="both", choices=["moves", "precondition", "both", "none"],
+                    help="Householder QR use (mps_options.qr): centre moves, the preconditioned gate SVD, "
+                         "both, or neither (Jacobi orthogonalisation)")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0, help="seconds of oracle work per CPU sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -262,7 +265,8 @@ def run_ours(a) -> int:
     qs = np.asarray(circ.qs, dtype=np.int32)
     stream = torch.cuda.current_stream(dev)
     m = E.MPS(a.n_qubits, f_min=a.f_min, n_2q=n, strategy=E.GLOBAL, chi_max=a.chi_cap, fixed_chi=a.fixed_chi,
-              precision=prec, log_truncations=False, stream=stream.cuda_stream, svd_kernel=svd_kernel_of(a, E))
+              precision=prec, log_truncations=False, stream=stream.cuda_stream, svd_kernel=svd_kernel_of(a, E),
+              qr=qr_of(a, E))
     flush = torch.empty(a.flush_mb * (1 << 20) // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -362,6 +366,8 @@ def run_ours(a) -> int:
         extras["time_to_target"] = time_to_target(E, torch, dev, a, prec)
         extras["chi512"] = chi512_throughput(E, torch, dev, a, prec, circ, ops_dev, qs)
         extras["precision_vs_fp64"] = precision_vs_fp64(E, a, prec, circ)
+        extras["batch"] = batch_block(E, torch, dev, a, prec)
+        extras["vidal_layers"] = vidal_layers_block(E, torch, dev, a, prec, circ, ops_dev, qs)
     extras["svd_layout_tuning"] = svd_tuning_summary(E)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -375,7 +381,8 @@ def run_ours(a) -> int:
                 "config": bench_config(a, n, world),
                 "inferred_fidelity": fid, "final_max_bond": max(bonds),
                 "wall_s_timed": wall, "gpu_launches": st["kernel_launches"], "roofline": roof,
-                "contraction": gemm, "householder_qr": qr, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk}
+                "contraction": gemm, "householder_qr": qr, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "options": {"svd_kernel": a.svd_kernel, "qr": a.qr}}
         line.update(extras)
         print(json.dumps(line), flush=True)
     m.close()
@@ -413,7 +420,7 @@ def time_to_target(E, torch, dev, a, prec) -> dict:
     n = circ.n_2q
     ops_dev = torch.from_numpy(circ.ops_array().view(np.float64).reshape(n, 32).copy()).to(dev)
     qs = np.asarray(circ.qs, dtype=np.int32)
-    kw = dict(precision=prec, svd_kernel=svd_kernel_of(a, E))
+    kw = dict(precision=prec, svd_kernel=svd_kernel_of(a, E), qr=qr_of(a, E))
     ea = [_timed_circuit(E, torch, dev, a.n_qubits, qs, ops_dev, 4, f_min=a.f_min, n_2q=n, strategy=E.GLOBAL,
                          chi_max=a.chi_cap, **kw) for _ in range(3)]
     chi = ea[0][2]
@@ -427,6 +434,59 @@ def time_to_target(E, torch, dev, a, prec) -> dict:
                    "reached_f_min": bool(ea[0][1] >= a.f_min)},
             "fixed_chi": {"chi": chi, "gpu_s": fx_s, "inferred_fidelity": fx[0][1]},
             "ea_time_over_fixed": ea_s / fx_s}
+
+
+def batch_block(E, torch, dev, a, prec, n_circuits: int = 16) -> dict:
+    """Many independent circuits through mps_batch_run: the first n_circuits of the batch study's
+    seeded mix (N ~ U[20, 80], depth ~ U[10, 30], F_min in {0.9, 0.99}, bond cap 128), one at a time
+    and eight at a time; wall time, host threads included.  Each circuit's result must be the same
+    at both concurrencies."""
+    specs = W.random_batch_specs(64, a.seed)[:n_circuits]
+    circs = [W.brickwork_circuit(sp["n_qubits"], sp["depth"], sp["seed"]) for sp in specs]
+    devs = [torch.from_numpy(c.ops_array().view(np.float64).reshape(c.n_2q, 32).copy()).to(dev) for c in circs]
+    total = sum(c.n_2q for c in circs)
+    items = [{"n_qubits": sp["n_qubits"], "qs": c.qs, "ops_dev": dv.data_ptr(), "op_dim": 4, "f_min": sp["f_min"],
+              "n_2q": c.n_2q, "chi_max": 128, "precision": prec} for sp, c, dv in zip(specs, circs, devs)]
+    E.mps_batch_run(items[:2], concurrency=2)   # warm-up
+    out = {"workload": f"{n_circuits} brickwork circuits, N ~ U[20, 80], depth ~ U[10, 30], F_min 0.9 / 0.99, "
+                       f"bond cap 128 ({total} gates)", "gates": total}
+    fids = {}
+    for conc in (1, 8):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        code, res = E.mps_batch_run(items, concurrency=conc)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        fids[conc] = [r["fidelity"] for r in res]
+        out[f"concurrency_{conc}"] = {"wall_s": dt, "updates_per_s": total / dt, "status": code}
+    out["speedup"] = out["concurrency_1"]["wall_s"] / out["concurrency_8"]["wall_s"]
+    out["same_results"] = fids[1] == fids[8]
+    return out
+
+
+def vidal_layers_block(E, torch, dev, a, prec, circ, ops_dev, qs, conc: int = 8) -> dict:
+    """The benchmark circuit in Vidal form, the gates of each brickwork layer concurrently
+    (mps_apply_layer_device, one schedule target per layer); wall time, host threads included."""
+    n = circ.n_2q
+    bounds = [0] + [g for g in range(1, n) if circ.layers[g] != circ.layers[g - 1]] + [n]
+    m = E.MPS(a.n_qubits, f_min=a.f_min, n_2q=n, strategy=E.GLOBAL, chi_max=a.chi_cap, precision=prec,
+              log_truncations=False, vidal=True)
+    m.apply_layer(qs[:1], ops_dev.data_ptr(), concurrency=conc)   # warm-up: helper handles
+    m.close()
+    m = E.MPS(a.n_qubits, f_min=a.f_min, n_2q=n, strategy=E.GLOBAL, chi_max=a.chi_cap, precision=prec,
+              log_truncations=False, vidal=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for a0, a1 in zip(bounds[:-1], bounds[1:]):
+        m.apply_layer(qs[a0:a1], ops_dev.data_ptr() + a0 * 256, concurrency=conc)
+    fid = m.fidelity()
+    dt = time.perf_counter() - t0
+    out = {"workload": f"same circuit, Vidal form, {len(bounds) - 1} layers, {conc} gates at a time",
+           "concurrency": conc, "wall_s": dt, "updates_per_s": n / dt, "inferred_fidelity": fid,
+           "max_bond": max(m.bond_dims()),
+           "note": "Vidal form: no canonical centre, so the inferred product is not a fidelity estimate here"}
+    m.close()
+    return out
 
 
 def svd_tuning_summary(E) -> dict:
@@ -444,12 +504,12 @@ def chi512_throughput(E, torch, dev, a, prec, circ, ops_dev, qs) -> dict:
     every saturated update is a 1024 x 1024 SVD."""
     n = circ.n_2q
     # the saturated 1024 x 1024 SVD's layout is tuned before the clock starts (once per process)
-    t = E.MPS(a.n_qubits, fixed_chi=512, chi_max=512, precision=prec, svd_kernel=svd_kernel_of(a, E))
+    t = E.MPS(a.n_qubits, fixed_chi=512, chi_max=512, precision=prec, svd_kernel=svd_kernel_of(a, E), qr=qr_of(a, E))
     for acc in (False, True):
         t.svd_tune(1024, 1024, acc)
     t.close()
     ms, fid, mx, jms, jl = _timed_circuit(E, torch, dev, a.n_qubits, qs, ops_dev, 4, n_2q=n, fixed_chi=512,
-                                          chi_max=512, precision=prec, svd_kernel=svd_kernel_of(a, E))
+                                          chi_max=512, precision=prec, svd_kernel=svd_kernel_of(a, E), qr=qr_of(a, E))
     return {"workload": f"same circuit, fixed chi = 512 ({n} gates)", "updates_per_s": n / (ms / 1e3),
             "gpu_s": ms / 1e3, "inferred_fidelity": fid, "max_bond": mx, "jacobi_share": jms / ms,
             "jacobi_ms_per_launch": jms / max(jl, 1)}
@@ -463,7 +523,7 @@ def precision_vs_fp64(E, a, prec, circ, n_prefix: int = 350) -> dict:
     runs = {}
     for name, pr in (("fp64", E.FP64), ("ours", prec)):
         m = E.MPS(a.n_qubits, f_min=a.f_min, n_2q=circ.n_2q, strategy=E.GLOBAL, chi_max=a.chi_cap, precision=pr,
-                  svd_kernel=svd_kernel_of(a, E))
+                  svd_kernel=svd_kernel_of(a, E), qr=qr_of(a, E))
         sv = []
         for g in range(n_prefix):
             q, u = circ.gates()[g]
@@ -824,6 +884,11 @@ def run_study(a) -> int:
     return 0
 
 
+def qr_of(a, E) -> int:
+    return {"moves": E.QR_MOVES, "precondition": E.QR_PRECONDITION, "both": E.QR_MOVES | E.QR_PRECONDITION,
+            "none": 0}[a.qr]
+
+
 def svd_kernel_of(a, E) -> int:
     return {"auto": E.SVD_AUTO, "tournament": E.SVD_TOURNAMENT, "gram": E.SVD_GRAM}[a.svd_kernel]
 
@@ -836,7 +901,8 @@ def run_micro(a) -> int:
     chi, n = a.micro, 24
     q = n // 2 - (a.steps + 1 if a.micro_moves else 0)
     sites, _ = W.random_canonical_mps(n, chi, q, seed=7)
-    m = E.MPS(n, chi_max=chi, fixed_chi=chi, precision=prec, log_truncations=False, svd_kernel=svd_kernel_of(a, E))
+    m = E.MPS(n, chi_max=chi, fixed_chi=chi, precision=prec, log_truncations=False, svd_kernel=svd_kernel_of(a, E),
+              qr=qr_of(a, E))
     m.load_sites(sites, q)
     m.profile(True)
     for g in range(max(a.steps, 1) + 1):

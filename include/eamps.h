@@ -82,15 +82,17 @@ typedef struct {
                            canonical form of Vidal), so the gates of a layer are independent.  The
                            truncation fidelity is exact only while the form stays canonical.  Default 0. */
   int svd_kernel;       /* layout of the one-sided Jacobi SVD (complex64; every layout computes the same
-                           rotations up to rounding): MPS_SVD_AUTO (default) the block kernel with Gram-matrix
-                           inner sweeps, one thread-block cluster per pair of 16-column blocks across the GPU,
-                           from 1024 columns on, else the tournament kernels; MPS_SVD_TOURNAMENT the
+                           rotations up to rounding): MPS_SVD_AUTO (default) the layout measured faster for the
+                           matrix's shape class (see mps_svd_tuning; where no timing was made: the block kernel
+                           with Gram-matrix inner sweeps, one thread-block cluster per pair of 16-column blocks
+                           across the GPU, from 1024 columns on, else the tournament kernels); MPS_SVD_TOURNAMENT the
                            cluster-resident / point-to-point tournament kernels only; MPS_SVD_GRAM the Gram
                            block kernel wherever a layout fits (64 columns and more). */
-  int qr;               /* Householder QR in the update (complex64), bit flags: MPS_QR_MOVES (default) moves the
-                           orthogonality centre by QR ("Canonicalization" section; otherwise by a Jacobi
-                           orthogonalisation), MPS_QR_PRECONDITION runs the gate SVD on the triangular factor
-                           of theta (fewer sweeps, one QR more). */
+  int qr;               /* Householder QR in the update (complex64), bit flags (default both): MPS_QR_MOVES
+                           moves the orthogonality centre by QR ("Canonicalization" section; otherwise by a
+                           Jacobi orthogonalisation), MPS_QR_PRECONDITION runs the gate SVD on the triangular
+                           factor of theta (fewer sweeps, one QR more).  Both apply to matrices of at most
+                           512 rows. */
 } mps_options;
 
 /* One record per two-qubit gate: bond size kept, truncation fidelity f, the

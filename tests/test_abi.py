@@ -48,7 +48,7 @@ def test_options_struct_layout_matches_header():
     assert ctypes.sizeof(E.TruncRecord) == 48
     # the library fills the struct: its last fields land where the binding reads them
     o = E.mps_default_options()
-    assert (o.max_sweeps, o.log_truncations, o.vidal, o.svd_kernel, o.qr) == (40, 1, 0, E.SVD_AUTO, E.QR_MOVES)
+    assert (o.max_sweeps, o.log_truncations, o.vidal, o.svd_kernel, o.qr) == (40, 1, 0, E.SVD_AUTO, E.QR_MOVES | E.QR_PRECONDITION)
 
 
 def test_superop_helper_matches_oracle():
