@@ -47,20 +47,20 @@ __device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.
 struct QrShared {
   float2 T[kQrPanel * kQrPanel];    // triangular factor of the current panel (row-major)
   float2 tau[kQrPanel];
-  float2 w[kQrPanel + 1];           // column products / scale of the current reflector
-  float red[1];   // beta of the current reflector
 };
 
 // The panel is factored by the kQrCluster CTAs of cluster 0: CTA r holds rows
 // [r * kQrPanelRows, (r + 1) * kQrPanelRows) of the panel, and each row is spread over four
 // threads of one warp (lane = 4 * row-in-warp + g), thread g holding columns [8 g, 8 g + 8) of the
-// row in registers.  Scratch layout (shared memory of each CTA): recv [2][kQrCluster][16 warps][32]
-// partial sums pushed by every warp of the cluster, by column parity; rowj [2][32] (row j of the
-// panel, pushed by CTA 0); then CTA 0's vg [32 x 32], vg[q * 32 + j] = (V^dagger V)[q][j] for
-// q < j, and M [32 x 32] for the merge of T.
+// row in registers.  Scratch layout (shared memory of each CTA), each part by column parity:
+// recv [2][kQrCluster][32], the 32 column sums of every panel CTA, pushed by their warp 0; red
+// [2][16 warps][32], this CTA's warp sums; rowj [2][32] (row j of the panel, pushed by CTA 0);
+// then CTA 0's vg [32 x 32], vg[q * 32 + j] = (V^dagger V)[q][j] for q < j, and M [32 x 32] for
+// the merge of T.
 constexpr int kQrWarps = kQrThreads / 32;
-constexpr int kQrRecv = kQrCluster * kQrWarps * 32;
-constexpr int kQrRowjOff = 2 * kQrRecv;
+constexpr int kQrRecv = kQrCluster * 32;
+constexpr int kQrRedOff = 2 * kQrRecv;
+constexpr int kQrRowjOff = kQrRedOff + 2 * kQrWarps * 32;
 constexpr int kQrVgOff = kQrRowjOff + 64;
 constexpr int kQrMOff = kQrVgOff + kQrPanel * kQrPanel;
 static_assert(kQrPanelRows * 4 == kQrThreads, "four threads per panel row");
@@ -131,51 +131,56 @@ __device__ __forceinline__ void panel_step(float2 (&a)[8], const PanelCtx& p, cg
   rs_round<4, 16>(v, lane);
   rs_round<2, 8>(v, lane);
   rs_round<1, 4>(v, lane);
-  // this lane now holds the warp's sum of slot 8 g + (lane >> 2): push it to every CTA
-  const int slot = 8 * g + (lane >> 2);
-#pragma unroll
-  for (int r = 0; r < kQrCluster; ++r) cl.map_shared_rank(recv, r)[(p.rank * kQrWarps + warp) * 32 + slot] = v[0];
-  cl.sync();
-  if (warp == 0) {   // every CTA forms the same scalars from the same sums, in the same order
-    float2 d4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll 16
-    for (int e = 0; e < kQrCluster * kQrWarps; ++e) d4[e & 3] = c_add(d4[e & 3], recv[e * 32 + lane]);
-    const float2 dc = c_add(c_add(d4[0], d4[1]), c_add(d4[2], d4[3]));
-    const float xn2 = __shfl_sync(0xffffffffu, dc.x, J);
-    const float2 alpha = rowj[J];
-    const float2 rl = rowj[lane];
-    float2 sc = make_float2(0.f, 0.f), tj = make_float2(0.f, 0.f);
-    float beta = alpha.x;
-    if (!(xn2 == 0.f && alpha.y == 0.f)) {
-      const float an = sqrt_nr(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-      beta = (alpha.x >= 0.f) ? -an : an;
-      const float ib = rcp_nr(beta);
-      tj = make_float2((beta - alpha.x) * ib, -alpha.y * ib);
-      const float2 den = make_float2(alpha.x - beta, alpha.y);          // scale = 1 / (alpha - beta)
-      const float idd = rcp_nr(den.x * den.x + den.y * den.y);
-      sc = make_float2(den.x * idd, -den.y * idd);
-    }
-    sh.w[lane] = (lane > J && lane < p.jb) ? c_add(rl, c_mul(c_conj(sc), dc)) : make_float2(0.f, 0.f);
-    if (p.rank == 0 && lane < J) p.scratch[kQrVgOff + lane * 32 + J] = c_add(c_mul(sc, dc), c_conj(rl));
-    if (lane == 0) {
-      sh.tau[J] = tj;
-      sh.w[kQrPanel] = sc;
-      sh.red[0] = beta;
-    }
-  }
+  // this lane now holds the warp's sum of slot 8 g + (lane >> 2); the CTA's sums then go to every
+  // panel CTA (warp 0 pushes them)
+  float2* red = p.scratch + kQrRedOff + par * (kQrWarps * 32);
+  red[warp * 32 + 8 * g + (lane >> 2)] = v[0];
   __syncthreads();
+  if (warp == 0) {
+    float2 d4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int w = 0; w < kQrWarps; ++w) d4[w & 3] = c_add(d4[w & 3], red[w * 32 + lane]);
+    const float2 ds = c_add(c_add(d4[0], d4[1]), c_add(d4[2], d4[3]));
+#pragma unroll
+    for (int r = 0; r < kQrCluster; ++r) cl.map_shared_rank(recv, r)[p.rank * 32 + lane] = ds;
+  }
+  cl.sync();
+  // every warp of every panel CTA forms the same scalars from the same sums, in the same order
+  // (lane = slot), so no broadcast and no further barrier is needed
+  const float2 dc = c_add(c_add(recv[lane], recv[32 + lane]), c_add(recv[64 + lane], recv[96 + lane]));
+  const float xn2 = __shfl_sync(0xffffffffu, dc.x, J);
+  const float2 alpha = rowj[J];
+  const float2 rl = rowj[lane];
+  float2 sc = make_float2(0.f, 0.f), tj = make_float2(0.f, 0.f);
+  float beta = alpha.x;
+  if (!(xn2 == 0.f && alpha.y == 0.f)) {
+    const float an = sqrt_nr(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+    beta = (alpha.x >= 0.f) ? -an : an;
+    const float ib = rcp_nr(beta);
+    tj = make_float2((beta - alpha.x) * ib, -alpha.y * ib);
+    const float2 den = make_float2(alpha.x - beta, alpha.y);          // scale = 1 / (alpha - beta)
+    const float idd = rcp_nr(den.x * den.x + den.y * den.y);
+    sc = make_float2(den.x * idd, -den.y * idd);
+  }
+  const float2 wl = (lane > J && lane < p.jb) ? c_add(rl, c_mul(c_conj(sc), dc)) : make_float2(0.f, 0.f);
+  if (p.rank == 0 && warp == 0) {
+    if (lane < J) p.scratch[kQrVgOff + lane * 32 + J] = c_add(c_mul(sc, dc), c_conj(rl));
+    if (lane == 0) sh.tau[J] = tj;
+  }
+  float2 wk[8];   // w of this thread's columns 8 g .. 8 g + 7
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    wk[k] = make_float2(__shfl_sync(0xffffffffu, wl.x, 8 * g + k), __shfl_sync(0xffffffffu, wl.y, 8 * g + k));
   // v = x * scale below the diagonal, R[J][J] = beta, and A[i][c] -= conj(tau) v_i w_c (w_c = 0
   // for c <= J, so those entries keep their values; entry J then takes v or beta)
   if (p.row >= J && p.row < p.nr) {
-    const float2 sc = sh.w[kQrPanel];
-    const float2 ctau = c_conj(sh.tau[J]);
     const bool diag = p.row == J;
     const float2 vv = diag ? make_float2(1.f, 0.f) : c_mul(x, sc);
-    const float2 nj = diag ? make_float2(sh.red[0], 0.f) : vv;
-    const float2 ctv = c_mul(ctau, vv);
+    const float2 nj = diag ? make_float2(beta, 0.f) : vv;
+    const float2 ctv = c_mul(c_conj(tj), vv);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const float2 u = c_sub(a[k], c_mul(ctv, sh.w[8 * g + k]));
+      const float2 u = c_sub(a[k], c_mul(ctv, wk[k]));
       a[k] = (8 * g + k == J) ? nj : u;
     }
   }
