@@ -207,6 +207,8 @@ struct Engine final : mps_state {
   cudaEvent_t ev_main = nullptr, ev_side = nullptr;
   Z* Xq = nullptr;      // the move's matrix, factored in place (R above the diagonal, reflectors below)
   Z* Qq = nullptr;      // its explicit Q
+  Z* Tq = nullptr;      // its block-reflector factors and tau (the gate's QR has its own)
+  Z* tauq = nullptr;
   bool side_pending = false;
   mps_options opt{};
   int sm_count = 1;
@@ -263,7 +265,7 @@ struct Engine final : mps_state {
     coop_release();
     if (!lam_owned) lam = nullptr;
     void* bufs[] = {arena, site_dev, bonds_dev, T, X, theta, Wacc, tmp, tmp2, G, O, s_sorted, norms, perm,
-                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T, lam, Xq, Qq};
+                    ctrl, wdev, w2dev, work, outdev, stage, xch, jflags, qr_tau, qr_T, lam, Xq, Qq, Tq, tauq};
     for (void* b : bufs) if (b) cudaFree(b);
     if (hctrl) cudaFreeHost(hctrl);
     if (hout) cudaFreeHost(hout);
@@ -452,7 +454,8 @@ struct Engine final : mps_state {
       if (qr_on && (!dalloc(&qr_tau, (size_t)c_max) || !dalloc(&qr_T, (size_t)1024 * ((c_max + 31) / 32))))
         return MPS_ERR_OOM;
       if (qr_on && (qr_mode & 2)) {
-        if (!dalloc(&Xq, (size_t)qr_max_rows() * c_max) || !dalloc(&Qq, (size_t)qr_max_rows() * qr_max_rows()))
+        if (!dalloc(&Xq, (size_t)qr_max_rows() * c_max) || !dalloc(&Qq, (size_t)qr_max_rows() * qr_max_rows()) ||
+            !dalloc(&Tq, (size_t)1024 * ((c_max + 31) / 32)) || !dalloc(&tauq, (size_t)c_max))
           return MPS_ERR_OOM;
         if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming) != cudaSuccess ||
@@ -599,14 +602,17 @@ struct Engine final : mps_state {
 
   // X (l x c, column-major, ld ldx) = Q R in place; with Q != nullptr also the explicit Q
   // (l x min(l, c), column-major, ld ldq).
-  mps_status qr_run(int l, int c, Z* Xp, long long ldx, Z* Q, long long ldq) {
-    if (mps_status s = join_side()) return s;   // qr_T and qr_tau may still be read there
+  // tmat, tvec: the block-reflector factors and tau (qr_T / qr_tau by default; a centre move whose
+  // Q is formed on the second stream passes its own, so the gate's QR need not wait for it)
+  mps_status qr_run(int l, int c, Z* Xp, long long ldx, Z* Q, long long ldq, Z* tmat = nullptr, Z* tvec = nullptr) {
+    if (!tmat) tmat = qr_T;
+    if (!tvec) tvec = qr_tau;
     if constexpr (std::is_same<R, float>::value) {
       const int ctas = qr_ctas(l, c, qr_fit);   // one cluster: no co-residency budget needed
       ++n_qr;
       const int id = tbegin();
-      mps_status s = kl(qr_factor(Xp, ldx, l, c, qr_tau, qr_T, ctrl, ctas, stream));
-      if (s == MPS_OK && Q) s = kl(qr_form_q(Xp, ldx, l, c, qr_T, Q, ldq, ctrl, qr_ctas(l, std::min(l, c), qr_fit), stream));
+      mps_status s = kl(qr_factor(Xp, ldx, l, c, tvec, tmat, ctrl, ctas, stream));
+      if (s == MPS_OK && Q) s = kl(qr_form_q(Xp, ldx, l, c, tmat, Q, ldq, ctrl, qr_ctas(l, std::min(l, c), qr_fit), stream));
       tend(id, 3);
       return s;
     } else {
@@ -624,7 +630,7 @@ struct Engine final : mps_state {
       if (mps_status s = cu(cudaEventRecord(ev_main, stream))) return s;
       if (mps_status s = cu(cudaStreamWaitEvent(side, ev_main, 0))) return s;
       const int id = tbegin(side);
-      mps_status s = kl(qr_form_q(QX, l, l, c, qr_T, Qq, l, ctrl, qr_ctas(l, std::min(l, c), qr_fit), side));
+      mps_status s = kl(qr_form_q(QX, l, l, c, Tq, Qq, l, ctrl, qr_ctas(l, std::min(l, c), qr_fit), side));
       tend(id, 3, side);
       if (s == MPS_OK)
         s = kl(extract_columns<R>(out, o_js, o_rs, kout, rows, Qq, l, 1, nullptr, conj, nullptr, 0, ctrl, side));
@@ -673,7 +679,7 @@ struct Engine final : mps_state {
       Z* QX = ovl ? Xq : X;
       if ((s = join_side())) return s;
       if ((s = extract(QX, m, 1, n, m, C, 1, n, nullptr, 0, nullptr, 0))) return s;      // QX = C column-major
-      if ((s = qr_run(m, n, QX, m, ovl ? nullptr : Wacc, m))) return s;                   // Q column-major
+      if ((s = qr_run(m, n, QX, m, ovl ? nullptr : Wacc, m, ovl ? Tq : nullptr, ovl ? tauq : nullptr))) return s;
       if (ovl && (s = side_q(m, n, QX, C, 1, K, K, m, 0))) return s;                      // A_c = Q row-major
       if ((s = kl(triu_extract<R>(tmp2, n, 1, QX, m, K, n, 0, stream)))) return s;         // R row-major K x n
       if ((s = gemm(K, n2, n, R(1), tmp2, n, 1, 0, Nx, n2, 1, 0, T, n2, 1))) return s;     // R A_{c+1}
@@ -720,7 +726,7 @@ struct Engine final : mps_state {
       Z* QX = ovl ? Xq : X;
       if ((s = join_side())) return s;
       if ((s = extract(QX, n, 1, m, n, C, n, 1, nullptr, 1, nullptr, 0))) return s;       // QX = C^dagger
-      if ((s = qr_run(n, m, QX, n, ovl ? nullptr : Wacc, n))) return s;                   // Q column-major n x K
+      if ((s = qr_run(n, m, QX, n, ovl ? nullptr : Wacc, n, ovl ? Tq : nullptr, ovl ? tauq : nullptr))) return s;
       // Q^dagger row-major (K x n): element (r, j) = conj(Q(j, r)) sits where Q(j, r) sits
       if (ovl && (s = side_q(n, m, QX, C, n, 1, K, n, 1))) return s;
       if ((s = kl(triu_extract<R>(tmp2, m, 1, QX, n, K, m, 0, stream)))) return s;         // R row-major K x m
