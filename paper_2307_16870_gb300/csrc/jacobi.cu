@@ -454,21 +454,29 @@ __device__ __forceinline__ void warp_allreduce(float (&v)[N], int lane) {
   for (int i = 0; i < N; ++i) v[i] = __shfl_sync(0xffffffffu, cur[0], i << (5 - LOG));
 }
 
-// The w*w cross pairs of one round.  Warp `warp` keeps A columns ia = warp*AP + a in
-// registers; at step t it takes B column w + (ia + t) mod w, which warp + 1 (mod NW)
-// released at step t - 1.  Returns the rotations applied by this warp.
-template <int NW, int RPL, int AP>
+// The w*w cross pairs of one round.  The NW warps form SP groups of NW / SP; warp pw of group h
+// keeps rows [h RPL / SP, (h + 1) RPL / SP) (per lane) of A columns ia = pw*AP + a in registers;
+// at step t it takes the same rows of B column w + (ia + t) mod w, which warp pw + 1 (mod NW / SP)
+// of its group released at step t - 1.  With SP > 1 the SP warps of a pair add their partial sums
+// through shared memory, in the same order, so that they apply the same rotation.  Returns the
+// rotations applied by this warp (counted by group 0 only).
+template <int NW, int RPL, int AP, int SP>
 __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int w, int kl, float tol, float tol_stop,
                                                 int lane, int warp, unsigned& big) {
   constexpr int ld = 32 * RPL;
-  float2 A[AP][RPL], B[AP][RPL];
+  constexpr int NP = NW / SP;    // pairs in flight (warps per group)
+  constexpr int RH = RPL / SP;   // rows per lane of one warp
+  static_assert(NP * SP == NW && RH * SP == RPL, "the row split divides warps and rows");
+  __shared__ float part[SP > 1 ? 2 : 1][NP * AP][SP][4];   // by step parity
+  const int pw = warp % NP, h = warp / NP, k0 = h * RH;
+  float2 A[AP][RH], B[AP][RH];
   int ib[AP];
 #pragma unroll
   for (int a = 0; a < AP; ++a) {
-    ib[a] = warp * AP + a;
+    ib[a] = pw * AP + a;
     const float2* src = slots + ib[a] * ld + lane;
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) A[a][k] = src[32 * k];
+    for (int k = 0; k < RH; ++k) A[a][k] = src[32 * (k0 + k)];
   }
   unsigned my_rot = 0;
   for (int t = 0; t < w; ++t) {
@@ -477,7 +485,7 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
     for (int a = 0; a < AP; ++a) {
       bcol[a] = slots + (w + ib[a]) * ld + lane;
 #pragma unroll
-      for (int k = 0; k < RPL; ++k) B[a][k] = bcol[a][32 * k];
+      for (int k = 0; k < RH; ++k) B[a][k] = bcol[a][32 * (k0 + k)];
     }
     // packed two-wide FP32: (u.re*u.re, u.im*u.im) style partial sums
     float2 d2a[AP], d2b[AP], g2a[AP], g2b[AP];
@@ -486,8 +494,8 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
       d2a[a] = make_float2(0.f, 0.f); d2b[a] = d2a[a]; g2a[a] = d2a[a]; g2b[a] = d2a[a];
     }
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) {
-      if (k < kl) {
+    for (int k = 0; k < RH; ++k) {
+      if (k0 + k < kl) {
 #pragma unroll
         for (int a = 0; a < AP; ++a) {
           const float2 u = A[a][k], v = B[a][k];
@@ -507,18 +515,34 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
       s[4 * a + 3] = g2b[a].x - g2b[a].y;      // Im(u^dagger v)
     }
     warp_allreduce<4 * AP>(s, lane);
+    if constexpr (SP > 1) {
+      float (*pt)[SP][4] = part[t & 1];
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 4 * AP; ++i) pt[pw * AP + i / 4][h][i % 4] = s[i];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4 * AP; ++i) {
+        float acc = pt[pw * AP + i / 4][0][i % 4];
+#pragma unroll
+        for (int hh = 1; hh < SP; ++hh) acc += pt[pw * AP + i / 4][hh][i % 4];
+        s[i] = acc;
+      }
+    }
 #pragma unroll
     for (int a = 0; a < AP; ++a) {
       float cs, al, be;
       if (rot_params_fused(s[4 * a], s[4 * a + 1], s[4 * a + 2], s[4 * a + 3], tol, cs, al, be)) {
-        big += (s[4 * a + 2] * s[4 * a + 2] + s[4 * a + 3] * s[4 * a + 3] >
-                tol_stop * tol_stop * s[4 * a] * s[4 * a + 1]) ? 1u : 0u;
+        if (h == 0)
+          big += (s[4 * a + 2] * s[4 * a + 2] + s[4 * a + 3] * s[4 * a + 3] >
+                  tol_stop * tol_stop * s[4 * a] * s[4 * a + 1]) ? 1u : 0u;
         // x' = cs x - sn e^{-i phi} y = cs x - al y - be (y.im, -y.re)
         // y' = sn e^{i phi} x + cs y = al x + be (-x.im, x.re) + cs y,  al + i be = sn e^{i phi}
         const float2 csv = make_float2(cs, cs), mal = make_float2(-al, -al), pal = make_float2(al, al);
         const float2 pbe = make_float2(-be, be);
 #pragma unroll
-        for (int k = 0; k < RPL; ++k) {
+        for (int k = 0; k < RH; ++k) {
           const float2 u = A[a][k], v = B[a][k];
           float2 nu = __fmul2_rn(u, csv);
           nu = __ffma2_rn(v, mal, nu);
@@ -527,9 +551,9 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
           nv = __ffma2_rn(u, pal, nv);
           nv = __ffma2_rn(make_float2(u.y, u.x), pbe, nv);
           A[a][k] = nu;
-          bcol[a][32 * k] = nv;
+          bcol[a][32 * (k0 + k)] = nv;
         }
-        ++my_rot;
+        if (h == 0) ++my_rot;
       }
       ib[a] = (ib[a] + 1 == w) ? 0 : ib[a] + 1;
     }
@@ -537,9 +561,9 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
   }
 #pragma unroll
   for (int a = 0; a < AP; ++a) {
-    float2* dst = slots + (warp * AP + a) * ld + lane;
+    float2* dst = slots + (pw * AP + a) * ld + lane;
 #pragma unroll
-    for (int k = 0; k < RPL; ++k) dst[32 * k] = A[a][k];
+    for (int k = 0; k < RH; ++k) dst[32 * (k0 + k)] = A[a][k];
   }
   return my_rot;
 }
@@ -582,7 +606,7 @@ __device__ __forceinline__ unsigned intra_phase(float2* slots, const int* gcol, 
 // Blocks move by bulk copies (one per block and direction): the publishing
 // thread drains its stores before the release, and the reading thread orders
 // its bulk load after the acquire with a proxy fence.
-template <class R, int NW, int RPL, int AP>
+template <class R, int NW, int RPL, int AP, int SP>
 __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
   static_assert(std::is_same<R, float>::value, "register-resident kernels are complex64");
   constexpr int ld = 32 * RPL;
@@ -674,7 +698,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_kernel3(JArgs<R> p) {
       }
       unsigned my_rot = 0, my_big = 0;
       if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, p.tol_stop, lane, warp, NW, my_big);
-      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, p.tol_stop, lane, warp, my_big);
+      my_rot += cross_phase<NW, RPL, AP, SP>(slots, w, kl, p.tol, p.tol_stop, lane, warp, my_big);
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
       if (lane == 0 && my_big) atomicAdd(&big_s, my_big);
       // shared-memory writes above must be visible to the bulk stores below
@@ -801,7 +825,7 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
     for (int r = 0; r < nb - 1; ++r) {
       unsigned my_rot = 0, my_big = 0;
       if (r == 0) my_rot += intra_phase(slots, gcol, w, ld, 32 * kl, p.tol, p.tol_stop, lane, warp, NW, my_big);
-      my_rot += cross_phase<NW, RPL, AP>(slots, w, kl, p.tol, p.tol_stop, lane, warp, my_big);
+      my_rot += cross_phase<NW, RPL, AP, 1>(slots, w, kl, p.tol, p.tol_stop, lane, warp, my_big);
       if (lane == 0 && my_rot) atomicAdd(&rot_s, my_rot);
       if (lane == 0 && my_big) atomicAdd(&big_s, my_big);
       __syncthreads();
@@ -880,10 +904,12 @@ __global__ void __launch_bounds__(NW * 32) jacobi_cluster_kernel(JArgs<R> p) {
   cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
 
-// Kernel variants of the register-resident form, indexed by (warps, rows per lane / 32, columns per warp).
-struct Variant { int nw, rpl, ap; const void* fn; };
+// Kernel variants of the register-resident form, indexed by (warps, rows per lane / 32, columns
+// per warp, warps sharing the rows of a column pair).  Block width w = nw / sp * ap.
+struct Variant { int nw, rpl, ap; const void* fn; int sp = 1; };
 
-#define EAMPS_V(NW, RPL, AP) {NW, RPL, AP, (const void*)jacobi_kernel3<float, NW, RPL, AP>}
+#define EAMPS_V(NW, RPL, AP) {NW, RPL, AP, (const void*)jacobi_kernel3<float, NW, RPL, AP, 1>}
+#define EAMPS_S(NW, RPL, AP, SP) {NW, RPL, AP, (const void*)jacobi_kernel3<float, NW, RPL, AP, SP>, SP}
 const Variant kVariants[] = {
     EAMPS_V(4, 4, 1),  EAMPS_V(8, 4, 1),  EAMPS_V(16, 4, 1),  EAMPS_V(8, 4, 2),  EAMPS_V(16, 4, 2),
     EAMPS_V(4, 8, 1),  EAMPS_V(8, 8, 1),  EAMPS_V(16, 8, 1),  EAMPS_V(4, 8, 2),  EAMPS_V(8, 8, 2), EAMPS_V(16, 8, 2),
@@ -891,8 +917,11 @@ const Variant kVariants[] = {
     EAMPS_V(4, 16, 1), EAMPS_V(8, 16, 1), EAMPS_V(16, 16, 1), EAMPS_V(4, 16, 2), EAMPS_V(8, 16, 2),
     EAMPS_V(4, 24, 1), EAMPS_V(8, 24, 1),
     EAMPS_V(4, 32, 1), EAMPS_V(8, 32, 1),
+    // rows split over two warps: 8 columns per block on 16 warps
+    EAMPS_S(16, 16, 1, 2), EAMPS_S(16, 8, 1, 2),
 };
 #undef EAMPS_V
+#undef EAMPS_S
 
 #define EAMPS_C(NW, RPL) {NW, RPL, 1, (const void*)jacobi_cluster_kernel<float, NW, RPL, 1>}
 const Variant kClusterVariants[] = {
@@ -907,9 +936,9 @@ const Variant* find_cluster_variant(int nw, int rpl) {
   return nullptr;
 }
 
-const Variant* find_variant(int nw, int rpl, int ap) {
+const Variant* find_variant(int nw, int rpl, int ap, int sp = 1) {
   for (const Variant& v : kVariants)
-    if (v.nw == nw && v.rpl == rpl && v.ap == ap) return &v;
+    if (v.nw == nw && v.rpl == rpl && v.ap == ap && v.sp == sp) return &v;
   return nullptr;
 }
 
@@ -1013,6 +1042,9 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
         P = (c + 2 * w - 1) / (2 * w);
       }
       nb = 2 * P;
+      // the same blocks on twice the warps: the rows of each column pair split over two warps
+      if (v->nw == 8 && v->ap == 1 && v->sp == 1)
+        if (const Variant* sv = find_variant(16, rpl, 1, 2)) v = sv;
     }
     const size_t smem = (size_t)2 * w * col_bytes + 2 * w * sizeof(int) + 16;
     if (v && smem <= 227 * 1024) {
