@@ -229,9 +229,10 @@ def run_reference(a) -> int:
 # DRAM traffic of one theta 512 x 512 launch of the point-to-point Jacobi kernel, from the ncu
 # capture named here (re-taken whenever that kernel changes; None when no capture of the current
 # kernel exists)
-TRAFFIC_512 = 2143232 + 48640
-TRAFFIC_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum of jacobi_kernel3 in an ncu capture of "
-                  "bench.py --micro 256 (profiles/jacobi_kernel3_theta512x512.md); not measured by this run")
+TRAFFIC_512 = 2141184 + 34816
+TRAFFIC_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum of jacobi_kernel3<float, 16, 16, 1, 2> (the "
+                  "row-split variant) in an ncu capture of bench.py --micro 256 --svd-kernel tournament "
+                  "(profiles/jacobi_kernel3_theta512x512.md); not measured by this run")
 
 
 def measured_peaks() -> dict:
