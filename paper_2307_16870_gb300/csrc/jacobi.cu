@@ -467,6 +467,7 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
   constexpr int NP = NW / SP;    // pairs in flight (warps per group)
   constexpr int RH = RPL / SP;   // rows per lane of one warp
   static_assert(NP * SP == NW && RH * SP == RPL, "the row split divides warps and rows");
+  static_assert(SP == 1 || NP <= 15, "one named barrier per pair");
   __shared__ float part[SP > 1 ? 2 : 1][NP * AP][SP][4];   // by step parity
   const int pw = warp % NP, h = warp / NP, k0 = h * RH;
   float2 A[AP][RH], B[AP][RH];
@@ -521,7 +522,8 @@ __device__ __forceinline__ unsigned cross_phase(float2* __restrict__ slots, int 
 #pragma unroll
         for (int i = 0; i < 4 * AP; ++i) pt[pw * AP + i / 4][h][i % 4] = s[i];
       }
-      __syncthreads();
+      // only the SP warps of this pair meet here (named barrier 1 + pw; 0 is the CTA barrier)
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + pw), "r"(32 * SP) : "memory");
 #pragma unroll
       for (int i = 0; i < 4 * AP; ++i) {
         float acc = pt[pw * AP + i / 4][0][i % 4];
