@@ -55,7 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--fixed-chi", type=int, default=0)
     ap.add_argument("--seed", type=int, default=1002)
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
-    ap.add_argument("--svd-kernel", default="auto", choices=["auto", "tournament", "gram"],
+    ap.add_argument("--svd-kernel", default="auto", choices=["auto", "tournament", "tournament-unsplit", "gram"],
                     help="layout of the Jacobi SVD (mps_options.svd_kernel)")
     ap.add_argument("--qr", default="both", choices=["moves", "precondition", "both", "none"],
                     help="Householder QR use (mps_options.qr): centre moves, the preconditioned gate SVD, "
@@ -494,10 +494,15 @@ def svd_tuning_summary(E) -> dict:
     """The Jacobi layout autotuner's choices so far in this process (shape classes of the SVD,
     rows and columns rounded up to 64): how many classes were timed and where each layout won."""
     tab = E.mps_svd_tuning()
-    gram = [f"{t['rows']}x{t['cols']}{'+W' if t['accumulate'] else ''}" for t in tab if t["layout"] == "gram"]
+
+    def names(layout):
+        return [f"{t['rows']}x{t['cols']}{'+W' if t['accumulate'] else ''}" for t in tab if t["layout"] == layout]
+
     ratios = [t["ms_gram"] / t["ms_tournament"] for t in tab if t["ms_gram"] > 0 and t["ms_tournament"] > 0]
-    return {"classes": len(tab), "gram_classes": gram,
-            "gram_over_tournament_time": {"min": min(ratios), "max": max(ratios)} if ratios else None}
+    split = [t["ms_tournament"] / t["ms_unsplit"] for t in tab if t["ms_unsplit"] > 0 and t["ms_tournament"] > 0]
+    return {"classes": len(tab), "gram_classes": names("gram"), "unsplit_classes": names("tournament_unsplit"),
+            "gram_over_tournament_time": {"min": min(ratios), "max": max(ratios)} if ratios else None,
+            "split_over_unsplit_time": {"min": min(split), "max": max(split)} if split else None}
 
 
 def chi512_throughput(E, torch, dev, a, prec, circ, ops_dev, qs) -> dict:
@@ -891,7 +896,8 @@ def qr_of(a, E) -> int:
 
 
 def svd_kernel_of(a, E) -> int:
-    return {"auto": E.SVD_AUTO, "tournament": E.SVD_TOURNAMENT, "gram": E.SVD_GRAM}[a.svd_kernel]
+    return {"auto": E.SVD_AUTO, "tournament": E.SVD_TOURNAMENT, "tournament-unsplit": E.SVD_TOURNAMENT_UNSPLIT,
+            "gram": E.SVD_GRAM}[a.svd_kernel]
 
 
 def run_micro(a) -> int:

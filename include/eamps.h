@@ -61,7 +61,8 @@ enum { MPS_PURE = 0, MPS_MIXED = 1 };                          /* mps_options.ki
 enum { MPS_NAIVE = 0, MPS_GLOBAL = 1, MPS_NEAREST = 2 };       /* mps_options.strategy */
 enum { MPS_FP64 = 0, MPS_TF32X3 = 1, MPS_FP32 = 2 };           /* mps_options.precision */
 enum { MPS_KEPT_RATIO = 0, MPS_WANG_SQRT = 1 };                /* mps_options.mixed_fid */
-enum { MPS_SVD_AUTO = 0, MPS_SVD_TOURNAMENT = 1, MPS_SVD_GRAM = 2 };  /* mps_options.svd_kernel */
+enum { MPS_SVD_AUTO = 0, MPS_SVD_TOURNAMENT = 1, MPS_SVD_GRAM = 2,
+       MPS_SVD_TOURNAMENT_UNSPLIT = 3 };                              /* mps_options.svd_kernel */
 enum { MPS_QR_PRECONDITION = 1, MPS_QR_MOVES = 2 };             /* mps_options.qr (bit flags) */
 
 typedef struct {
@@ -86,8 +87,10 @@ typedef struct {
                            matrix's shape class (see mps_svd_tuning; where no timing was made: the block kernel
                            with Gram-matrix inner sweeps, one thread-block cluster per pair of 16-column blocks
                            across the GPU, from 1024 columns on, else the tournament kernels); MPS_SVD_TOURNAMENT the
-                           cluster-resident / point-to-point tournament kernels only; MPS_SVD_GRAM the Gram
-                           block kernel wherever a layout fits (64 columns and more). */
+                           cluster-resident / point-to-point tournament kernels only (the point-to-point
+                           kernel at 256 and 512 rows with the rows of each column pair split over two warps);
+                           MPS_SVD_TOURNAMENT_UNSPLIT the same with one warp per column pair; MPS_SVD_GRAM the
+                           Gram block kernel wherever a layout fits (64 columns and more). */
   int qr;               /* Householder QR in the update (complex64), bit flags (default both): MPS_QR_MOVES
                            moves the orthogonality centre by QR ("Canonicalization" section; otherwise by a
                            Jacobi orthogonalisation), MPS_QR_PRECONDITION runs the gate SVD on the triangular
@@ -187,16 +190,20 @@ mps_status mps_apply_layer_device(mps_handle h, int n_gates, const int* qs, cons
 /* The Jacobi layout autotuner's table for the current device (this process).
  * Under MPS_SVD_AUTO, the first time a handle that runs alone meets a shape
  * class of the SVD's matrix (rows and columns rounded up to multiples of 64,
- * whether rotations are accumulated) with at least 256 columns, both layouts of
- * the one-sided Jacobi are timed on a synthetic matrix of the shape it met; the
- * Gram block layout is kept for the class when it is at least 10 % faster.
- * Fills up to `cap` entries (class rows and columns, accumulated rotations 0/1,
- * chosen layout MPS_SVD_TOURNAMENT / MPS_SVD_GRAM, or MPS_SVD_AUTO when neither
- * could be timed and the fixed size rule applies, and the two times in ms, -1
- * where a layout does not apply) and returns the number of entries (-1 on a
+ * whether rotations are accumulated) with at least 256 columns, the layouts
+ * of the one-sided Jacobi are timed:
+ * the tournament kernels with and without the row split (the faster is kept)
+ * and the Gram block layout, kept when it is at least 10 % faster still, each
+ * on a copy of the matrix about to be decomposed (mps_svd_tune: on a
+ * synthetic matrix).
+ * Fills up to `cap` entries (class rows and columns, accumulated rotations
+ * 0/1, chosen layout MPS_SVD_TOURNAMENT / MPS_SVD_TOURNAMENT_UNSPLIT /
+ * MPS_SVD_GRAM, or MPS_SVD_AUTO when nothing could be timed and the fixed size
+ * rule applies, and the three times in ms, -1 where a layout does not apply or
+ * is the same launch as another) and returns the number of entries (-1 on a
  * CUDA error).  With cap 0 and null pointers it only counts.  Host only. */
 int mps_svd_tuning(int cap, int* rows, int* cols, int* accumulate, int* layout, double* ms_tournament,
-                   double* ms_gram);
+                   double* ms_gram, double* ms_unsplit);
 
 /* Tune the Jacobi layout of one shape class ahead of use (the timing runs the
  * autotuner would otherwise make inside the first SVD of that class, see

@@ -35,7 +35,7 @@ PURE, MIXED = 0, 1
 NAIVE, GLOBAL, NEAREST = 0, 1, 2
 FP64, TF32X3, FP32 = 0, 1, 2
 KEPT_RATIO, WANG_SQRT = 0, 1
-SVD_AUTO, SVD_TOURNAMENT, SVD_GRAM = 0, 1, 2
+SVD_AUTO, SVD_TOURNAMENT, SVD_GRAM, SVD_TOURNAMENT_UNSPLIT = 0, 1, 2, 3
 QR_PRECONDITION, QR_MOVES = 1, 2
 SELFTEST_FLAG, SELFTEST_JACOBI, SELFTEST_GRAM, SELFTEST_GEMM = 0, 1, 2, 3
 
@@ -140,7 +140,8 @@ def load(path: str | None = None):
         "mps_selftest_timeout": (C.c_int, [H, C.c_int, C.c_longlong]),
         "mps_svd_tune": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
         "mps_svd_tuning": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                     C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
         "mps_schedule_target": (C.c_int, [C.c_int, C.c_double, C.c_longlong, C.c_longlong, C.c_double,
                                           C.POINTER(C.c_double)]),
     }
@@ -255,15 +256,16 @@ def mps_tsvd_backward_device(h: int, m: int, n: int, k: int, u: int, s: int, v: 
 def mps_svd_tuning() -> list[dict]:
     """The Jacobi layout autotuner's table for the current device (see include/eamps.h)."""
     lib = load()
-    n = lib.mps_svd_tuning(0, None, None, None, None, None, None)
+    n = lib.mps_svd_tuning(0, None, None, None, None, None, None, None)
     if n <= 0:
         return []
     ib = [(C.c_int * n)() for _ in range(4)]
-    db = [(C.c_double * n)() for _ in range(2)]
+    db = [(C.c_double * n)() for _ in range(3)]
     lib.mps_svd_tuning(n, *ib, *db)
-    names = {SVD_TOURNAMENT: "tournament", SVD_GRAM: "gram", SVD_AUTO: "rule"}
+    names = {SVD_TOURNAMENT: "tournament", SVD_GRAM: "gram", SVD_TOURNAMENT_UNSPLIT: "tournament_unsplit",
+             SVD_AUTO: "rule"}
     return [{"rows": ib[0][i], "cols": ib[1][i], "accumulate": bool(ib[2][i]), "layout": names.get(ib[3][i], "?"),
-             "ms_tournament": db[0][i], "ms_gram": db[1][i]} for i in range(n)]
+             "ms_tournament": db[0][i], "ms_gram": db[1][i], "ms_unsplit": db[2][i]} for i in range(n)]
 
 
 def mps_schedule_target(strategy: int, f_min: float, n_2q: int, n_done: int, product: float) -> float:

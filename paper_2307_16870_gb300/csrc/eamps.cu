@@ -73,12 +73,14 @@ double schedule_target(int strategy, double f_min, long long n_2q, long long n_d
 
 // ---------------------------------------------------------------- Jacobi layout autotuner
 // The first time a handle meets a shape class (rows and columns rounded up to kTuneGrain,
-// accumulation) with at least kTuneMinCols columns under MPS_SVD_AUTO, it times both layouts of
-// the one-sided Jacobi (the tournament kernels and the Gram-matrix block kernel) on a synthetic
-// matrix of the shape it met and keeps the faster one for the process (the block kernel only when
-// at least 10 % faster, so that near ties do not flip between runs).  Every real SVD of that class
-// then runs the chosen layout.  The classes keep the number of timing runs small on circuits whose
-// bonds take many values.
+// accumulation) with at least kTuneMinCols columns under MPS_SVD_AUTO, it times the layouts of the
+// one-sided Jacobi (the tournament kernels with and without the row split, and the Gram-matrix
+// block kernel) on copies of the matrix it is about to decompose and keeps the fastest for the
+// process (the block kernel only when at least 10 % faster, so that near ties do not flip between
+// runs).  Every later SVD of that class runs the chosen layout.  The classes keep the number of
+// timing runs small on circuits whose bonds take many values.  (A synthetic matrix, the first
+// form of this tuner, picked the unsplit tournament at 512 columns, 12-21 % faster there, while
+// the split form is about 3 % faster on the benchmark's own matrices.)
 constexpr int kTuneMinCols = 256;
 constexpr int kTuneGrain = 64;
 struct TuneKey {
@@ -92,7 +94,7 @@ struct TuneKey {
 };
 struct TuneEntry {
   int kind;
-  double ms_tournament, ms_gram;
+  double ms_tournament, ms_gram, ms_unsplit;
 };
 std::mutex& tune_mutex() {
   static std::mutex m;
@@ -505,7 +507,8 @@ struct Engine final : mps_state {
       const int fit = plan.cluster > 0 ? plan.cluster : jacobi_max_ctas<R>(plan);
       if (fit <= 0) return MPS_ERR_CUDA;
       if (plan.nb / 2 > fit) {
-        plan = jacobi_plan<R>(l, c, acc, sm_count, fit, MPS_SVD_TOURNAMENT);
+        plan = jacobi_plan<R>(l, c, acc, sm_count, fit,
+                              kind == MPS_SVD_TOURNAMENT_UNSPLIT ? MPS_SVD_TOURNAMENT_UNSPLIT : MPS_SVD_TOURNAMENT);
         if (plan.nb / 2 > fit) return MPS_ERR_ARG;
       }
     }
@@ -513,8 +516,10 @@ struct Engine final : mps_state {
   }
 
   // The layout kind for a shape: the option, or under MPS_SVD_AUTO the tuned choice (measured on
-  // first use of the shape when this handle runs alone on the GPU; the fixed rule otherwise).
-  int layout_for(int l, int c, bool acc, bool force = false) {
+  // first use of the shape when this handle runs alone on the GPU; the fixed rule otherwise).  The
+  // timing runs take copies of src (l x c, column-major, ld lds: the matrix about to be
+  // decomposed) when given, else a synthetic matrix.
+  int layout_for(int l, int c, bool acc, bool force = false, const Z* src = nullptr, long long lds = 0) {
     if (!std::is_same<R, float>::value || opt.svd_kernel != MPS_SVD_AUTO || c < kTuneMinCols) return opt.svd_kernel;
     const auto up = [](int v) { return (v + kTuneGrain - 1) / kTuneGrain * kTuneGrain; };
     const TuneKey key{device, up(l), up(c), acc ? 1 : 0};
@@ -524,20 +529,26 @@ struct Engine final : mps_state {
       if (it != tune_table().end()) return it->second.kind;
     }
     if (shared_gpu && !force) return MPS_SVD_AUTO;   // no timing runs beside other handles' kernels
-    double ms[2] = {-1.0, -1.0};
-    const int kinds[2] = {MPS_SVD_TOURNAMENT, MPS_SVD_GRAM};
+    double ms[3] = {-1.0, -1.0, -1.0};
+    const int kinds[3] = {MPS_SVD_TOURNAMENT, MPS_SVD_GRAM, MPS_SVD_TOURNAMENT_UNSPLIT};
+    const void* split_fn = nullptr;
     const long long nx = (long long)l * c, nw = acc ? (long long)c * c : 0;
     Z* xt = nullptr;
     DevCtrl* tc = nullptr;
     cudaEvent_t e0 = ev_get(), e1 = ev_get();
     if (cudaMalloc(&xt, sizeof(Z) * (nx + nw + 1)) == cudaSuccess && cudaMalloc(&tc, sizeof(DevCtrl)) == cudaSuccess) {
-      for (int v = 0; v < 2; ++v) {
+      for (int v = 0; v < 3; ++v) {
         JacobiPlan plan;
         if (make_plan(l, c, acc, kinds[v], plan) != MPS_OK) continue;
         if (kinds[v] == MPS_SVD_GRAM && plan.gram_R == 0) continue;
+        if (v == 0) split_fn = plan.fn;
+        if (v == 2 && plan.fn == split_fn) continue;   // no split variant for this shape: the same launch
         double best = -1.0;
         for (int rep = 0; rep < 2; ++rep) {
-          synthetic_fill_kernel<<<256, 256, 0, stream>>>(reinterpret_cast<float2*>(xt), nx, 12345u);
+          if (src)
+            cudaMemcpy2DAsync(xt, sizeof(Z) * l, src, sizeof(Z) * lds, sizeof(Z) * l, c, cudaMemcpyDeviceToDevice, stream);
+          else
+            synthetic_fill_kernel<<<256, 256, 0, stream>>>(reinterpret_cast<float2*>(xt), nx, 12345u);
           if (acc) set_identity<R>(xt + nx, c, c, stream);
           cudaMemsetAsync(tc, 0, sizeof(DevCtrl), stream);
           cudaEventRecord(e0, stream);
@@ -559,11 +570,14 @@ struct Engine final : mps_state {
     if (tc) cudaFree(tc);
     ev_pool.push_back(e0);
     ev_pool.push_back(e1);
+    // the faster tournament form, then the block layout only when at least 10 % faster than it
     int kind = MPS_SVD_TOURNAMENT;
-    if (ms[1] > 0.0 && (ms[0] < 0.0 || ms[1] < 0.9 * ms[0])) kind = MPS_SVD_GRAM;
-    if (ms[0] < 0.0 && ms[1] < 0.0) kind = MPS_SVD_AUTO;   // no measurement: the fixed rule
+    double tbest = ms[0];
+    if (ms[2] > 0.0 && (tbest < 0.0 || ms[2] < tbest)) { kind = MPS_SVD_TOURNAMENT_UNSPLIT; tbest = ms[2]; }
+    if (ms[1] > 0.0 && (tbest < 0.0 || ms[1] < 0.9 * tbest)) kind = MPS_SVD_GRAM;
+    if (ms[0] < 0.0 && ms[1] < 0.0 && ms[2] < 0.0) kind = MPS_SVD_AUTO;   // no measurement: the fixed rule
     std::lock_guard<std::mutex> lk(tune_mutex());
-    auto ins = tune_table().emplace(key, TuneEntry{kind, ms[0], ms[1]});
+    auto ins = tune_table().emplace(key, TuneEntry{kind, ms[0], ms[1], ms[2]});
     return ins.first->second.kind;
   }
 
@@ -585,7 +599,7 @@ struct Engine final : mps_state {
       if (mps_status s = kl(set_identity<R>(Wacc, c, c, stream))) return s;
     if (c <= 1) return MPS_OK;
     JacobiPlan plan;
-    if (mps_status s = make_plan(l, c, acc, layout_for(l, c, acc), plan)) return s;
+    if (mps_status s = make_plan(l, c, acc, layout_for(l, c, acc, false, Xp, ldx), plan)) return s;
     plan.early_stop = early_stop;
     if (mps_status s = coop_ensure(jacobi_plan_ctas(plan))) return s;
     ++n_jac;
@@ -1513,7 +1527,7 @@ mps_status mps_create(mps_handle* out, int n_qubits, const mps_options* opt, voi
   if (!(opt->f_min > 0.0) || opt->strategy < 0 || opt->strategy > 2 || opt->chi_max < 0 || opt->fixed_chi < 0 ||
       opt->precision < 0 || opt->precision > 2 || opt->mixed_fid < 0 || opt->mixed_fid > 1 || opt->max_sweeps < 1 ||
       opt->n_2q < 0 || opt->chi_max > 4096 || opt->vidal < 0 || opt->vidal > 1 || opt->svd_kernel < 0 ||
-      opt->svd_kernel > 2 || opt->qr < 0 || opt->qr > 3 ||
+      opt->svd_kernel > 3 || opt->qr < 0 || opt->qr > 3 ||
       (opt->vidal && opt->kind != MPS_PURE))
     return MPS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1730,20 +1744,21 @@ mps_status mps_tsvd_backward_device(mps_handle h, int m, int n, int k, const voi
 }
 
 int mps_svd_tuning(int cap, int* rows, int* cols, int* accumulate, int* layout, double* ms_tournament,
-                   double* ms_gram) {
+                   double* ms_gram, double* ms_unsplit) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   std::lock_guard<std::mutex> lk(tune_mutex());
   int n = 0;
   for (const auto& kv : tune_table()) {
     if (kv.first.dev != dev) continue;
-    if (n < cap && rows && cols && accumulate && layout && ms_tournament && ms_gram) {
+    if (n < cap && rows && cols && accumulate && layout && ms_tournament && ms_gram && ms_unsplit) {
       rows[n] = kv.first.l;
       cols[n] = kv.first.c;
       accumulate[n] = kv.first.acc;
       layout[n] = kv.second.kind;
       ms_tournament[n] = kv.second.ms_tournament;
       ms_gram[n] = kv.second.ms_gram;
+      ms_unsplit[n] = kv.second.ms_unsplit;
     }
     ++n;
   }

@@ -979,7 +979,8 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
   JacobiPlan plan;
   const int L = l + (accumulate ? c : 0);
   // block Jacobi with Gram-matrix inner sweeps over clusters across the GPU (jacobi_gram.cu)
-  if (std::is_same<R, float>::value && kind != kJacobiTournament && c >= (kind == kJacobiGram ? 64 : kGramMinCols) &&
+  if (std::is_same<R, float>::value && kind != kJacobiTournament && kind != kJacobiTournamentUnsplit &&
+      c >= (kind == kJacobiGram ? 64 : kGramMinCols) &&
       jacobi_gram_plan(l, c, accumulate, std::min(sm_count, max_ctas), plan))
     return plan;
   const size_t budget = 200 * 1024;
@@ -1045,7 +1046,7 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
       }
       nb = 2 * P;
       // the same blocks on twice the warps: the rows of each column pair split over two warps
-      if (v->nw == 8 && v->ap == 1 && v->sp == 1)
+      if (kind != kJacobiTournamentUnsplit && v->nw == 8 && v->ap == 1 && v->sp == 1)
         if (const Variant* sv = find_variant(16, rpl, 1, 2)) v = sv;
     }
     const size_t smem = (size_t)2 * w * col_bytes + 2 * w * sizeof(int) + 16;

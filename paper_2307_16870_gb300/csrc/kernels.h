@@ -76,7 +76,10 @@ struct JacobiPlan {
 // (the Gram-matrix block kernel whenever a layout fits, from 64 columns on).  Measured on GB300
 // (complex64, square theta): the two layouts take the same time at 512 columns (7.7 ms, 13 sweeps)
 // and the Gram kernel wins at 1024 (21.2 ms against 24.9 ms); below 512 the tournament kernels win.
-enum { kJacobiAuto = 0, kJacobiTournament = 1, kJacobiGram = 2 };
+// kJacobiTournamentUnsplit: the tournament kernels with one warp per column pair throughout
+// (kJacobiTournament splits the rows of each pair over two warps in the point-to-point kernel at
+// 256 and 512 rows).
+enum { kJacobiAuto = 0, kJacobiTournament = 1, kJacobiGram = 2, kJacobiTournamentUnsplit = 3 };
 constexpr int kGramMinCols = 1024;
 template <class R>
 JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas, int kind = kJacobiAuto);

@@ -24,7 +24,7 @@ from tests.helpers import contract_sites  # noqa: E402
 if E is not None:
     from paper_2307_16870_gb300 import autodiff as AD  # noqa: E402
 
-LAYOUTS = [("gram", 2), ("tournament", 1)]
+LAYOUTS = [("gram", 2), ("tournament", 1), ("tournament_unsplit", 3)]
 
 
 @pytest.mark.parametrize("name,kernel", LAYOUTS)
@@ -88,19 +88,25 @@ def test_accumulated_rotations_match_the_oracle(m, n, ws_gram):
     assert np.abs(aq @ ap - r["Aq"] @ r["Ap"]).max() < 1e-5 * np.abs(r["Aq"] @ r["Ap"]).max() * 10
 
 
-def test_autotuner_times_both_layouts_and_keeps_the_faster():
+def test_autotuner_times_the_layouts_and_keeps_the_faster():
     """mps_svd_tune on a 512 x 512 class (with and without accumulated rotations): the table then
-    holds both timings, and the kept layout is the block kernel exactly when it was at least 10 %
-    faster.  A second call does not time again."""
+    holds the timings, the kept tournament form is the faster of the two (with and without the row
+    split, where both exist), and the block kernel is kept exactly when it was at least 10 % faster
+    than that.  A second call does not time again."""
     m = E.MPS(100, chi_max=256, precision=E.TF32X3)
     for acc in (False, True):
         layout = m.svd_tune(512, 512, acc)
-        assert layout in (E.SVD_TOURNAMENT, E.SVD_GRAM)
+        assert layout in (E.SVD_TOURNAMENT, E.SVD_TOURNAMENT_UNSPLIT, E.SVD_GRAM)
     tab = {(t["rows"], t["cols"], t["accumulate"]): t for t in E.mps_svd_tuning()}
     for acc in (False, True):
         t = tab[(512, 512, acc)]
         assert t["ms_tournament"] > 0 and t["ms_gram"] > 0
-        assert (t["layout"] == "gram") == (t["ms_gram"] < 0.9 * t["ms_tournament"])
+        tours = [x for x in (t["ms_tournament"], t["ms_unsplit"]) if x > 0]
+        best = min(tours)
+        assert (t["layout"] == "gram") == (t["ms_gram"] < 0.9 * best)
+        if t["layout"] != "gram":
+            want = "tournament_unsplit" if 0 < t["ms_unsplit"] < t["ms_tournament"] else "tournament"
+            assert t["layout"] == want
     # the class of 500 x 470 is that of 512 x 512: no new timing run
     before = len(E.mps_svd_tuning())
     m.svd_tune(500, 470, False)
