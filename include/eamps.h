@@ -94,8 +94,8 @@ typedef struct {
   int qr;               /* Householder QR in the update (complex64), bit flags (default both): MPS_QR_MOVES
                            moves the orthogonality centre by QR ("Canonicalization" section; otherwise by a
                            Jacobi orthogonalisation), MPS_QR_PRECONDITION runs the gate SVD on the triangular
-                           factor of theta (fewer sweeps, one QR more).  Both apply to matrices of at most
-                           512 rows. */
+                           factor of theta (fewer sweeps, one QR more) when its shorter side has at least
+                           256 columns.  Both apply to matrices of at most 512 rows. */
 } mps_options;
 
 /* One record per two-qubit gate: bond size kept, truncation fidelity f, the

@@ -82,6 +82,9 @@ double schedule_target(int strategy, double f_min, long long n_2q, long long n_d
 // form of this tuner, picked the unsplit tournament at 512 columns, 12-21 % faster there, while
 // the split form is about 3 % faster on the benchmark's own matrices.)
 constexpr int kTuneMinCols = 256;
+// The QR-preconditioned gate SVD from this many columns of the Jacobi's matrix on (below it the
+// QR's fixed latency outweighs the sweeps it saves).
+constexpr int kPrecondMinCols = 256;
 constexpr int kTuneGrain = 64;
 struct TuneKey {
   int dev, l, c, acc;   // l, c: upper bounds of the class
@@ -851,7 +854,7 @@ struct Engine final : mps_state {
     else mode = (m <= n) ? L_ROWS : L_COLS_ACC;
     // QR preconditioning when the wanted directions are the right singular vectors of a tall X:
     // X = theta^dagger (n >= m) for a rightward update, X = theta (m >= n) for a leftward one
-    const bool use_qr = (qr_mode & 1) && std::min(m, n) >= 2 && (right ? n >= m : m >= n) &&
+    const bool use_qr = (qr_mode & 1) && std::min(m, n) >= kPrecondMinCols && (right ? n >= m : m >= n) &&
                         qr_ok(std::max(m, n), std::min(m, n));
     const bool cols = use_qr ? !right : (mode == R_COLS || mode == L_COLS_ACC);   // X = theta (else theta^dagger)
     const int l = cols ? m : n, c = cols ? n : m;
