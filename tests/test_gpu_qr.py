@@ -96,8 +96,34 @@ def test_circuit_with_qr_modes_matches_oracle(mode):
     f_orc = abs(np.vdot(psi, o.to_statevector())) ** 2
     assert abs(f_true - f_orc) < 1e-4
     st = m.stats()
-    if mode == 0:
-        assert st["qr_launches"] == 0
-    else:
+    if mode & E.QR_MOVES:
         assert st["qr_launches"] > 0
+    else:   # bonds <= 64 here: the gate SVD is preconditioned only from 256 columns on
+        assert st["qr_launches"] == 0
+    m.close()
+
+
+@pytest.mark.parametrize("centre,q", [(20, 20), (20, 21)])
+def test_preconditioned_update_from_256_columns(centre, q):
+    """The QR-preconditioned gate SVD at its smallest size (theta 256 x 256, bonds 128) in both
+    orientations, against the oracle's LAPACK SVD on identical inputs: same k, retained singular
+    values to 1e-5 relative."""
+    import workloads as W
+    from oracle import textbook_mps as T
+    n, cap = 40, 128
+    sites, _ = W.random_canonical_mps(n, cap, centre, seed=600 + q)
+    u = W.haar_unitary(4, 601, q)
+    orc = T.TextbookMPS(n, record_svals=True, chi_max=cap)
+    orc.sites = [x.copy() for x in sites]
+    orc.centre = centre
+    rec = orc.apply_2q(q, u, target=0.999)
+    m = E.MPS(n, chi_max=cap, precision=E.TF32X3, qr=E.QR_PRECONDITION)
+    m.load_sites(sites, centre)
+    m.stats_reset()
+    m.apply_2q(q, u, 0.999)
+    k = rec["k"]
+    assert m.truncation_log()[-1]["k"] == k
+    rel = np.abs(m.last_singular_values()[:k] - rec["s"][:k]) / rec["s"][:k]
+    assert rel.max() < 1e-5, rel.max()
+    assert m.stats()["qr_launches"] >= 1
     m.close()
