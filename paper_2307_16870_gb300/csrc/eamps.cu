@@ -505,13 +505,14 @@ struct Engine final : mps_state {
   // Launch plan of one Jacobi SVD for a layout kind, with the co-residency check of the
   // tournament kernels (the Gram layout is checked when it is planned).
   mps_status make_plan(int l, int c, bool acc, int kind, JacobiPlan& plan) {
-    plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count, kind);
+    const int ns = shared_gpu ? kJacobiNoSplit : 0;   // beside other handles: no 512-thread CTAs
+    plan = jacobi_plan<R>(l, c, acc, sm_count, sm_count, kind | ns);
     if (plan.gram_R == 0) {
       const int fit = plan.cluster > 0 ? plan.cluster : jacobi_max_ctas<R>(plan);
       if (fit <= 0) return MPS_ERR_CUDA;
       if (plan.nb / 2 > fit) {
         plan = jacobi_plan<R>(l, c, acc, sm_count, fit,
-                              kind == MPS_SVD_TOURNAMENT_UNSPLIT ? MPS_SVD_TOURNAMENT_UNSPLIT : MPS_SVD_TOURNAMENT);
+                              (kind == MPS_SVD_TOURNAMENT_UNSPLIT ? MPS_SVD_TOURNAMENT_UNSPLIT : MPS_SVD_TOURNAMENT) | ns);
         if (plan.nb / 2 > fit) return MPS_ERR_ARG;
       }
     }
@@ -524,6 +525,9 @@ struct Engine final : mps_state {
   // decomposed) when given, else a synthetic matrix.
   int layout_for(int l, int c, bool acc, bool force = false, const Z* src = nullptr, long long lds = 0) {
     if (!std::is_same<R, float>::value || opt.svd_kernel != MPS_SVD_AUTO || c < kTuneMinCols) return opt.svd_kernel;
+    // a handle that runs beside others keeps the fixed rule: the table was measured alone, and a
+    // layout that spans the GPU (the block kernel) would serialise the concurrent handles
+    if (shared_gpu && !force) return MPS_SVD_AUTO;
     const auto up = [](int v) { return (v + kTuneGrain - 1) / kTuneGrain * kTuneGrain; };
     const TuneKey key{device, up(l), up(c), acc ? 1 : 0};
     {
@@ -531,7 +535,6 @@ struct Engine final : mps_state {
       auto it = tune_table().find(key);
       if (it != tune_table().end()) return it->second.kind;
     }
-    if (shared_gpu && !force) return MPS_SVD_AUTO;   // no timing runs beside other handles' kernels
     double ms[3] = {-1.0, -1.0, -1.0};
     const int kinds[3] = {MPS_SVD_TOURNAMENT, MPS_SVD_GRAM, MPS_SVD_TOURNAMENT_UNSPLIT};
     const void* split_fn = nullptr;

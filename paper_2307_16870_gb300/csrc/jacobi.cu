@@ -977,6 +977,8 @@ int jacobi_max_ctas(const JacobiPlan& plan) {
 template <class R>
 JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas, int kind) {
   JacobiPlan plan;
+  const bool no_split = (kind & kJacobiNoSplit) != 0 || (kind & 7) == kJacobiTournamentUnsplit;
+  kind &= 7;
   const int L = l + (accumulate ? c : 0);
   // block Jacobi with Gram-matrix inner sweeps over clusters across the GPU (jacobi_gram.cu)
   if (std::is_same<R, float>::value && kind != kJacobiTournament && kind != kJacobiTournamentUnsplit &&
@@ -1046,7 +1048,7 @@ JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas
       }
       nb = 2 * P;
       // the same blocks on twice the warps: the rows of each column pair split over two warps
-      if (kind != kJacobiTournamentUnsplit && v->nw == 8 && v->ap == 1 && v->sp == 1)
+      if (!no_split && v->nw == 8 && v->ap == 1 && v->sp == 1)
         if (const Variant* sv = find_variant(16, rpl, 1, 2)) v = sv;
     }
     const size_t smem = (size_t)2 * w * col_bytes + 2 * w * sizeof(int) + 16;

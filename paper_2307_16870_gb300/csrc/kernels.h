@@ -79,7 +79,9 @@ struct JacobiPlan {
 // kJacobiTournamentUnsplit: the tournament kernels with one warp per column pair throughout
 // (kJacobiTournament splits the rows of each pair over two warps in the point-to-point kernel at
 // 256 and 512 rows).
-enum { kJacobiAuto = 0, kJacobiTournament = 1, kJacobiGram = 2, kJacobiTournamentUnsplit = 3 };
+// kJacobiNoSplit (a flag added to any kind): no row split either (a handle that runs beside others:
+// the split variant's 512-thread CTAs hold a whole SM's registers and leave no room for the others').
+enum { kJacobiAuto = 0, kJacobiTournament = 1, kJacobiGram = 2, kJacobiTournamentUnsplit = 3, kJacobiNoSplit = 8 };
 constexpr int kGramMinCols = 1024;
 template <class R>
 JacobiPlan jacobi_plan(int l, int c, bool accumulate, int sm_count, int max_ctas, int kind = kJacobiAuto);
