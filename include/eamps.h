@@ -84,9 +84,11 @@ typedef struct {
                            truncation fidelity is exact only while the form stays canonical.  Default 0. */
   int svd_kernel;       /* layout of the one-sided Jacobi SVD (complex64; every layout computes the same
                            rotations up to rounding): MPS_SVD_AUTO (default) the layout measured faster for the
-                           matrix's shape class (see mps_svd_tuning; where no timing was made: the block kernel
+                           matrix's shape class (see mps_svd_tuning); where no timing was made, and always in a
+                           handle that runs beside others (batch, Vidal layers), the fixed rule: the block kernel
                            with Gram-matrix inner sweeps, one thread-block cluster per pair of 16-column blocks
-                           across the GPU, from 1024 columns on, else the tournament kernels); MPS_SVD_TOURNAMENT the
+                           across the GPU, from 1024 columns on, else the tournament kernels (beside others
+                           without the row split); MPS_SVD_TOURNAMENT the
                            cluster-resident / point-to-point tournament kernels only (the point-to-point
                            kernel at 256 and 512 rows with the rows of each column pair split over two warps);
                            MPS_SVD_TOURNAMENT_UNSPLIT the same with one warp per column pair; MPS_SVD_GRAM the
