@@ -119,3 +119,19 @@ def test_schedule_target_matches_the_oracle_schedule():
                 o.n_done += 1
     with pytest.raises(E.MpsError):
         E.mps_schedule_target(5, 0.9, 10, 0, 1.0)
+
+
+def test_option_ranges_are_checked_without_touching_the_gpu():
+    """mps_options.svd_kernel accepts the four layouts (AUTO, TOURNAMENT, GRAM, TOURNAMENT_UNSPLIT)
+    and mps_options.qr the four bit combinations; values outside are refused with MPS_ERR_ARG
+    before any device work."""
+    import ctypes as C
+    import paper_2307_16870_gb300 as E
+    lib = E.load()
+    for field, bad in (("svd_kernel", 4), ("svd_kernel", -1), ("qr", 4), ("qr", -1)):
+        o = E.MpsOptions()
+        lib.mps_default_options(C.byref(o))
+        setattr(o, field, bad)
+        h = C.c_void_p()
+        assert lib.mps_create(C.byref(h), 8, C.byref(o), None) == 1, (field, bad)
+    assert E.SVD_TOURNAMENT_UNSPLIT == 3 and E.QR_MOVES | E.QR_PRECONDITION == 3
